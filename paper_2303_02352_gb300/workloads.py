@@ -1,0 +1,244 @@
+"""Seeded synthetic workloads: the 3D diffusion matrices and right-hand sides.
+
+This module is the only code shared by the CPU oracle and the CUDA path.  It
+builds inputs and holds none of the solver's arithmetic (no matching, no
+Galerkin product, no smoothing, no Krylov step).
+
+Problems (Sec. 5, the benchmark equation -div(K grad u) = f on the unit cube
+with homogeneous Dirichlet conditions, discretised by finite differences):
+
+* ``poisson7(N)``: K = 1, the classic 7-point stencil scaled by h^2, i.e. the
+  integer stencil (6, -1).  Scaling A and b by the same constant changes none of
+  the iterates of the method, so the integer form keeps every value exact.
+* ``diffusion7(N, sigma, seed)``: 7-point stencil with a cellwise coefficient
+  k = exp(sigma * g), g a standard Gaussian that is constant on 8^3 blocks.  The
+  link coefficient between neighbouring cells is the harmonic mean
+  2 k_i k_j / (k_i + k_j); a link that leaves the domain uses k_i.
+* ``diffusion27(N, sigma, seed)``: 27-point stencil with the same coefficient
+  field; the link to neighbour offset d carries the harmonic mean divided by
+  |d|^2 (1, 2 or 3 for face, edge and corner neighbours).
+
+The paper has no variable-coefficient or 27-point case; those two families are
+defined here for the mixed-precision and learned-smoother studies.
+
+Unknowns are numbered lexicographically, i = x + N*y + N^2*z, boundary
+unknowns eliminated.  Every matrix is returned as CSR with int32 row pointers
+and column indices (columns ascending within a row, diagonal included) and
+float64 values, and is bitwise symmetric by construction (each link value is
+computed by an expression symmetric in its two cells).
+
+Random numbers: a counter-based SplitMix64 stream.  ``splitmix64(seed, i)`` is
+the i-th output (i = 0, 1, ...) of Steele, Lea and Flood's SplitMix64 generator
+started from state ``seed``: state_i = seed + (i + 1) * 0x9E3779B97F4A7C15,
+followed by the published 64-bit finaliser.  U[0,1) takes the top 53 bits.
+Gaussians use the Box-Muller transform of draws 2b and 2b+1.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, idx: np.ndarray) -> np.ndarray:
+    """Outputs number ``idx`` of SplitMix64 seeded with ``seed`` (uint64 array)."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + (idx + np.uint64(1)) * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, idx) -> np.ndarray:
+    """U[0,1) from the top 53 bits of the SplitMix64 output."""
+    z = splitmix64(seed, np.asarray(idx, dtype=np.uint64))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def gaussian(seed: int, idx) -> np.ndarray:
+    """Standard normal number ``idx`` of stream ``seed`` (Box-Muller, cosine branch)."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    u1 = uniform01(seed, np.uint64(2) * idx)
+    u2 = uniform01(seed, np.uint64(2) * idx + np.uint64(1))
+    return np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * math.pi * u2)
+
+
+@dataclass
+class CSR:
+    """A square sparse matrix in CSR form (int32 indices, float64 values)."""
+    n: int
+    row_ptr: np.ndarray
+    col_idx: np.ndarray
+    val: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def to_scipy(self):
+        import scipy.sparse as sp
+        return sp.csr_matrix((self.val, self.col_idx, self.row_ptr), shape=(self.n, self.n))
+
+
+def _offsets(points: int):
+    if points == 7:
+        offs = [(0, 0, -1), (0, -1, 0), (-1, 0, 0), (0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    elif points == 27:
+        offs = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    else:
+        raise ValueError("points must be 7 or 27")
+    # ascending linear offset dz*N^2 + dy*N + dx gives ascending columns (N >= 3)
+    return sorted(offs, key=lambda d: (d[2], d[1], d[0]))
+
+
+def block_field(N: int, sigma: float, seed: int, block: int = 8) -> np.ndarray:
+    """Cellwise coefficient k = exp(sigma * g_B), g_B ~ N(0,1) per block^3 block."""
+    nb = -(-N // block)
+    g = gaussian(seed, np.arange(nb ** 3, dtype=np.uint64))
+    kb = np.exp(sigma * g)
+    c = np.arange(N) // block
+    bz, by, bx = np.meshgrid(c, c, c, indexing="ij")
+    return kb[(bx + nb * by + nb * nb * bz).ravel()]
+
+
+def _stencil(N: int, points: int, kcell: np.ndarray | None, zchunk: int | None = None) -> CSR:
+    if N < 3:
+        raise ValueError("N must be >= 3")
+    n = N ** 3
+    offs = _offsets(points)
+    L = len(offs)
+    plane = N * N
+    if zchunk is None:
+        zchunk = max(1, min(N, (1 << 24) // plane))
+    counts = np.empty(n, dtype=np.int64)
+    cols_parts, vals_parts = [], []
+    xs = np.arange(N)
+    for z0 in range(0, N, zchunk):
+        z1 = min(N, z0 + zchunk)
+        zz, yy, xx = np.meshgrid(np.arange(z0, z1), xs, xs, indexing="ij")
+        xx, yy, zz = xx.ravel(), yy.ravel(), zz.ravel()
+        i = xx + N * yy + plane * zz
+        m = i.size
+        cols = np.empty((m, L), dtype=np.int64)
+        vals = np.zeros((m, L), dtype=np.float64)
+        mask = np.zeros((m, L), dtype=bool)
+        diag_pos = offs.index((0, 0, 0))
+        diag = np.zeros(m, dtype=np.float64)
+        ki = None if kcell is None else kcell[i]
+        for p, (dx, dy, dz) in enumerate(offs):
+            if (dx, dy, dz) == (0, 0, 0):
+                cols[:, p] = i
+                mask[:, p] = True
+                continue
+            d2 = float(dx * dx + dy * dy + dz * dz)
+            a, b, c = xx + dx, yy + dy, zz + dz
+            inside = (a >= 0) & (a < N) & (b >= 0) & (b < N) & (c >= 0) & (c < N)
+            j = i + dx + N * dy + plane * dz
+            cols[:, p] = j
+            mask[:, p] = inside
+            if kcell is None:
+                link = np.ones(m)
+                link_out = np.ones(m)
+            else:
+                kj = kcell[np.where(inside, j, i)]
+                link = (2.0 * (ki * kj)) / (ki + kj)
+                link_out = ki
+            if d2 != 1.0:
+                link = link / d2
+                link_out = link_out / d2
+            vals[:, p] = np.where(inside, -link, 0.0)
+            diag = diag + np.where(inside, link, link_out)
+        vals[:, diag_pos] = diag
+        counts[i] = mask.sum(axis=1)
+        cols_parts.append(cols[mask].astype(np.int32))
+        vals_parts.append(vals[mask])
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    if row_ptr[-1] >= 2 ** 31:
+        raise ValueError("nnz does not fit int32")
+    return CSR(n, row_ptr.astype(np.int32), np.concatenate(cols_parts), np.concatenate(vals_parts))
+
+
+def poisson7(N: int) -> CSR:
+    """7-point Poisson on an N^3 grid, integer stencil (6, -1) (Sec. 5 benchmark)."""
+    if N < 3:
+        raise ValueError("N must be >= 3")
+    return _stencil(N, 7, None)
+
+
+def diffusion7(N: int, sigma: float, seed: int, block: int = 8) -> CSR:
+    """7-point variable-coefficient diffusion with log-normal blockwise k."""
+    return _stencil(N, 7, block_field(N, sigma, seed, block))
+
+
+def diffusion27(N: int, sigma: float, seed: int, block: int = 8) -> CSR:
+    """27-point variable-coefficient diffusion with log-normal blockwise k."""
+    return _stencil(N, 27, block_field(N, sigma, seed, block))
+
+
+def laplace1d(n: int) -> CSR:
+    """1D Dirichlet Laplacian tridiag(-1, 2, -1) of order n."""
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    i = np.arange(n)
+    cols, vals, counts = [], [], np.zeros(n, dtype=np.int64)
+    c = np.stack([i - 1, i, i + 1], axis=1)
+    v = np.tile(np.array([-1.0, 2.0, -1.0]), (n, 1))
+    mask = (c >= 0) & (c < n)
+    counts = mask.sum(axis=1)
+    row_ptr = np.zeros(n + 1, dtype=np.int32)
+    row_ptr[1:] = np.cumsum(counts)
+    return CSR(n, row_ptr, c[mask].astype(np.int32), v[mask])
+
+
+def random_vector(n: int, seed: int) -> np.ndarray:
+    """x_i = 2 U_i - 1 with U from stream ``seed``."""
+    return 2.0 * uniform01(seed, np.arange(n, dtype=np.uint64)) - 1.0
+
+
+def rhs_from_solution(A: CSR, xstar: np.ndarray) -> np.ndarray:
+    """b = A x* (input preparation for problems with a known solution)."""
+    prod = A.val * xstar[A.col_idx]
+    return np.add.reduceat(prod, A.row_ptr[:-1].astype(np.int64)) if A.n else np.zeros(0)
+
+
+def training_sigma(p: int) -> float:
+    """Log-normal sigma of training problem p: 0.5 + 2.5 U, U drawn far from the field stream."""
+    return 0.5 + 2.5 * float(uniform01(1000 + p, np.array([1 << 40], dtype=np.uint64))[0])
+
+
+def training_problem(p: int, N: int = 64) -> CSR:
+    """Training problem p of the learned smoother: 7-point, log-normal k, seed 1000+p."""
+    return diffusion7(N, training_sigma(p), 1000 + p)
+
+
+def config(name: str):
+    """Named workloads.  Returns (A, b, description)."""
+    if name == "poisson32":
+        A = poisson7(32)
+        return A, rhs_from_solution(A, random_vector(A.n, 1)), "7-pt Poisson 32^3, b = A x*, x* ~ U(-1,1) seed 1"
+    if name == "poisson160":
+        A = poisson7(160)
+        return A, rhs_from_solution(A, random_vector(A.n, 2)), "7-pt Poisson 160^3, b = A x*, x* ~ U(-1,1) seed 2"
+    if name == "diffusion27_128":
+        A = diffusion27(128, 2.0, 3)
+        return A, rhs_from_solution(A, random_vector(A.n, 3)), "27-pt log-normal diffusion 128^3, sigma 2, seed 3"
+    if name == "diffusion7_256":
+        A = diffusion7(256, 2.0, 4000)
+        return A, rhs_from_solution(A, random_vector(A.n, 4)), "7-pt log-normal diffusion 256^3, sigma 2, seed 4000"
+    if name == "poisson320":
+        A = poisson7(320)
+        return A, rhs_from_solution(A, random_vector(A.n, 5)), "7-pt Poisson 320^3, b = A x*, x* ~ U(-1,1) seed 5"
+    m = __import__("re").fullmatch(r"poisson(\d+)", name)
+    if m:
+        N = int(m.group(1))
+        A = poisson7(N)
+        return A, rhs_from_solution(A, random_vector(A.n, N)), f"7-pt Poisson {N}^3, seed {N}"
+    raise KeyError(name)
