@@ -1,0 +1,165 @@
+/*
+ * libamg: GB300 (sm_103a) aggregation-based AMG-preconditioned flexible CG.
+ *
+ * The method is the solver of arXiv:2303.02352 ("BootCMatchGX"): the flexible
+ * preconditioned CG of Alg. 1 driven by the V-cycle of Alg. 2 (operator B^k of
+ * Sec. 3.1) with l1-Jacobi smoothing (Sec. 3.1), built by the coarsening of
+ * Alg. 3 (pairwise aggregation from a half-approximate maximum-weight matching,
+ * s pairwise steps composed into aggregates of at most 2^s rows, Galerkin
+ * coarse operators).  Every step runs in this library's CUDA kernels on one GPU.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are square CSR with int32 row pointers and column indices,
+ *    columns strictly ascending within a row, the diagonal stored, values
+ *    float64; the matrix must be symmetric bit for bit (a_ij == a_ji) with a
+ *    positive diagonal (SPD is required by the method and not checked beyond).
+ *  - "device" pointers are CUDA global-memory pointers on the current device;
+ *    "host" pointers are CPU memory (pinned memory makes copies faster).
+ *  - All work is enqueued on the stream given to amg_setup (NULL = legacy
+ *    default stream).  Every call returns only after that stream has finished
+ *    the call's work, unless stated otherwise.
+ *  - The caller owns all buffers it passes; the library copies what it keeps.
+ *    The handle owns the hierarchy, work vectors and CUDA graphs until
+ *    amg_destroy.  A handle must not be used by two threads at once.
+ *  - Errors are returned as negative amg_status codes; no exception crosses the
+ *    ABI.  amg_last_error gives a one-line description of the last failure.
+ */
+#ifndef AMG_H
+#define AMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AMG_OK = 0,
+  AMG_NOT_CONVERGED = 1,     /* maxit reached; x and the history are still valid */
+  AMG_ERR_INVALID_ARG = -1,  /* bad pointer, size, or matrix structure */
+  AMG_ERR_NOT_SPD = -2,      /* non-positive diagonal */
+  AMG_ERR_BREAKDOWN = -3,    /* rho <= 0 or not finite in Alg. 1; x holds the last good iterate */
+  AMG_ERR_CUDA = -4,         /* a CUDA runtime call failed */
+  AMG_ERR_OOM = -5,          /* device allocation failed */
+  AMG_ERR_TIMEOUT = -6,      /* a bounded device loop hit its iteration cap */
+  AMG_ERR_TOO_LARGE = -7     /* size beyond what an entry point supports */
+} amg_status;
+
+typedef enum { AMG_FP64 = 0, AMG_FP32 = 1, AMG_FP32_BF16FINE = 2 } amg_precision;
+
+/* CSR matrix in device memory (see conventions above). */
+typedef struct {
+  int32_t n;
+  int32_t nnz;
+  const int32_t* row_ptr; /* device, n+1 */
+  const int32_t* col_idx; /* device, nnz */
+  const double* val;      /* device, nnz */
+} amg_csr;
+
+/* Parameters; amg_params_default gives the settings of Sec. 5 / Listing 1. */
+typedef struct {
+  int32_t aggr_steps;     /* s: pairwise matching steps composed per level (3 -> aggregates <= 8) */
+  int32_t max_levels;     /* maximum number of hierarchy levels (39) */
+  int32_t coarse_size;    /* stop coarsening once n <= coarse_size; 0 -> 40*round(cbrt(n)) */
+  int32_t pre_sweeps;     /* l1-Jacobi pre-smoothing sweeps (4) */
+  int32_t post_sweeps;    /* l1-Jacobi post-smoothing sweeps (4) */
+  int32_t coarse_sweeps;  /* l1-Jacobi sweeps on the coarsest level (20) */
+  int32_t precision;      /* amg_precision of the hierarchy inside the V-cycle (AMG_FP64) */
+  int32_t true_res_every; /* low precision: r <- b - A u every k iterations (50); 0 = never */
+  int32_t use_graph;      /* 1: replay the V-cycle and the FCG iteration as CUDA graphs (1) */
+  int32_t graph_batch;    /* FCG iterations launched between two convergence reads (4) */
+} amg_params;
+
+typedef struct {
+  int32_t num_levels;
+  int32_t n[40];          /* rows per level */
+  int64_t nnz[40];        /* nonzeros per level */
+  double opc;             /* operator complexity: sum nnz / nnz of level 0 (Sec. 5) */
+  int32_t num_pairwise;   /* pairwise matching steps performed in the setup */
+  double setup_ms;        /* wall time of amg_setup */
+  double vcycle_bytes;    /* algorithmic bytes one V-cycle moves (each kernel's reads and writes) */
+  double iteration_bytes; /* algorithmic bytes of one FCG iteration (V-cycle + outer kernels) */
+  int32_t vcycle_launches;    /* kernel launches of one V-cycle */
+  int32_t iteration_launches; /* kernel launches of one FCG iteration */
+  int32_t precision;          /* amg_precision of the hierarchy */
+} amg_info_t;
+
+typedef struct amg_handle amg_handle;
+
+/* Fills *p with the defaults above. */
+void amg_params_default(amg_params* p);
+
+/*
+ * Builds the hierarchy on the GPU (Alg. 3, Sec. 3.1): matching weights, suitor
+ * matching with an index tie-break, pairwise aggregation, Galerkin products,
+ * s-fold composition, l1-Jacobi diagonals, low-precision copies.
+ * A: device CSR, read during the call only (deep-copied).  p: NULL = defaults.
+ * stream: a cudaStream_t (may be NULL).  *out receives the handle.
+ * Errors: AMG_ERR_INVALID_ARG (structure, asymmetry, NaN), AMG_ERR_NOT_SPD
+ * (diagonal <= 0), AMG_ERR_OOM, AMG_ERR_CUDA, AMG_ERR_TIMEOUT.
+ */
+amg_status amg_setup(const amg_csr* A, const amg_params* p, void* stream, amg_handle** out);
+
+/*
+ * Alg. 1 (flexible PCG, one V-cycle per iteration) on A u = b.
+ * b: device, n.  x: device, n; in: initial guess u_0, out: solution.
+ * Stops when |r|_2/|b|_2 < tol after an update (confirmed on the true residual
+ * b - A u) or after maxit iterations.  iters (host, may be NULL): number of
+ * updates of u.  res_hist (host, may be NULL, length maxit+1): |r_i|/|b| for
+ * i = 0..iters.  true_rel_res (host, may be NULL): |b - A u|/|b| at exit.
+ * Returns AMG_OK, AMG_NOT_CONVERGED, AMG_ERR_BREAKDOWN or an error.
+ */
+amg_status amg_pcg_solve(amg_handle* h, const double* b, double* x, double tol, int32_t maxit,
+                         int32_t* iters, double* res_hist, double* true_rel_res);
+
+/* Same as amg_pcg_solve with b and x in host memory: the host-to-device copy of
+ * b and x and the device-to-host copy of x are part of the call. */
+amg_status amg_pcg_solve_host(amg_handle* h, const double* b_host, double* x_host, double tol,
+                              int32_t maxit, int32_t* iters, double* res_hist, double* true_rel_res);
+
+/* Plain CG (Alg. 1 with B = I, the paper's precflag = 0); same arguments. */
+amg_status amg_cg_solve(amg_handle* h, const double* b, double* x, double tol, int32_t maxit,
+                        int32_t* iters, double* res_hist, double* true_rel_res);
+
+/* One application of the preconditioner, z = B r (Alg. 2).  r, z: device, n,
+ * distinct buffers. */
+amg_status amg_vcycle(amg_handle* h, const double* r, double* z);
+
+/* y = A^k x for hierarchy level k.  x, y: device, n_k, distinct buffers. */
+amg_status amg_spmv(amg_handle* h, int32_t level, const double* x, double* y);
+
+/* Hierarchy summary (host struct). */
+amg_status amg_info(const amg_handle* h, amg_info_t* info);
+
+/* Copies of the hierarchy to host memory.  agg_host: n_k ints, the level-k row
+ * -> level-(k+1) row map (level < num_levels-1).  CSR: n_k+1, nnz_k, nnz_k. */
+amg_status amg_get_aggregates(amg_handle* h, int32_t level, int32_t* agg_host);
+amg_status amg_get_level_csr(amg_handle* h, int32_t level, int32_t* row_ptr_host,
+                             int32_t* col_idx_host, double* val_host);
+/* l1 row norms M_ii = sum_j |a_ij| of level k (host, n_k doubles). */
+amg_status amg_get_l1(amg_handle* h, int32_t level, double* l1_host);
+
+/*
+ * Measurement helpers (for benchmarking; results in milliseconds).
+ * amg_time_vcycle: average time of one V-cycle over reps replays.
+ * amg_time_kernel: average duration of one launch of kernel `which` on `level`
+ *   over reps launches, timed with CUDA events on the handle's stream:
+ *   0 = l1-Jacobi sweep, 1 = residual, 2 = restriction, 3 = prolongation,
+ *   4 = outer SpMV fused with the dot products, 5 = fused axpys.
+ */
+amg_status amg_time_vcycle(amg_handle* h, int32_t reps, double* ms);
+amg_status amg_time_kernel(amg_handle* h, int32_t which, int32_t level, int32_t reps, double* ms);
+/* bytes: host double; the algorithmic bytes of one launch of `which` on `level`
+ * (values, column indices, row pointers and vector entries each counted once). */
+amg_status amg_kernel_bytes(const amg_handle* h, int32_t which, int32_t level, double* bytes);
+/* Last error message of the handle (or of the last failed amg_setup if h is NULL). */
+const char* amg_last_error(const amg_handle* h);
+
+/* Frees everything the handle owns.  NULL is ignored. */
+void amg_destroy(amg_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMG_H */

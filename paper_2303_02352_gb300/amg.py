@@ -1,0 +1,262 @@
+"""Thin Python binding of libamg (the C ABI declared in include/amg.h).
+
+Argument marshalling only: every step of the setup and the solve runs in the
+library's CUDA kernels.  PyTorch provides device memory and the stream.  If the
+library has not been built, loading fails with an error (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_HERE, "_build", "libamg.so")
+
+OK, NOT_CONVERGED = 0, 1
+ERR_INVALID_ARG, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_TOO_LARGE = -1, -2, -3, -4, -5, -6, -7
+FP64, FP32, FP32_BF16FINE = 0, 1, 2
+K_SWEEP, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_SPMV_DOTS, K_AXPY = range(6)
+
+_STATUS = {0: "AMG_OK", 1: "AMG_NOT_CONVERGED", -1: "AMG_ERR_INVALID_ARG", -2: "AMG_ERR_NOT_SPD",
+           -3: "AMG_ERR_BREAKDOWN", -4: "AMG_ERR_CUDA", -5: "AMG_ERR_OOM", -6: "AMG_ERR_TIMEOUT",
+           -7: "AMG_ERR_TOO_LARGE"}
+
+
+class AmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class amg_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+PARAM_FIELDS = ("aggr_steps", "max_levels", "coarse_size", "pre_sweeps", "post_sweeps", "coarse_sweeps",
+                "precision", "true_res_every", "use_graph", "graph_batch")
+
+
+class amg_params(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int32) for f in PARAM_FIELDS]
+
+
+class amg_info_t(ctypes.Structure):
+    _fields_ = [("num_levels", ctypes.c_int32), ("n", ctypes.c_int32 * 40), ("nnz", ctypes.c_int64 * 40),
+                ("opc", ctypes.c_double), ("num_pairwise", ctypes.c_int32), ("setup_ms", ctypes.c_double),
+                ("vcycle_bytes", ctypes.c_double), ("iteration_bytes", ctypes.c_double),
+                ("vcycle_launches", ctypes.c_int32), ("iteration_launches", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
+
+
+_LIB = None
+
+
+def load(path: str | None = None):
+    """Loads libamg.so (raises if it is missing: there is no fallback path)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or SO_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libamg.so not found at {path}: build it with paper_2303_02352_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I32, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    I32P, DP = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "amg_params_default": (None, [ctypes.POINTER(amg_params)]),
+        "amg_setup": (I32, [ctypes.POINTER(amg_csr), ctypes.POINTER(amg_params), P, ctypes.POINTER(P)]),
+        "amg_pcg_solve": (I32, [P, P, P, D, I32, I32P, DP, DP]),
+        "amg_pcg_solve_host": (I32, [P, P, P, D, I32, I32P, DP, DP]),
+        "amg_cg_solve": (I32, [P, P, P, D, I32, I32P, DP, DP]),
+        "amg_vcycle": (I32, [P, P, P]),
+        "amg_spmv": (I32, [P, I32, P, P]),
+        "amg_info": (I32, [P, ctypes.POINTER(amg_info_t)]),
+        "amg_get_aggregates": (I32, [P, I32, P]),
+        "amg_get_level_csr": (I32, [P, I32, P, P, P]),
+        "amg_get_l1": (I32, [P, I32, P]),
+        "amg_time_vcycle": (I32, [P, I32, DP]),
+        "amg_time_kernel": (I32, [P, I32, I32, I32, DP]),
+        "amg_kernel_bytes": (I32, [P, I32, I32, DP]),
+        "amg_last_error": (ctypes.c_char_p, [P]),
+        "amg_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def params_default(**overrides) -> amg_params:
+    p = amg_params()
+    load().amg_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k not in PARAM_FIELDS:
+            raise KeyError(f"unknown parameter {k}")
+        setattr(p, k, int(v))
+    return p
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+class Hierarchy:
+    """An AMG hierarchy on the GPU (handle of amg_setup) and its solve phase.
+
+    ``A``: a CSR with ``n``, ``row_ptr``, ``col_idx``, ``val`` (numpy or torch;
+    copied to the GPU) or a ``torch.sparse_csr_tensor`` of float64 on CUDA.
+    Keyword arguments override the fields of ``amg_params``.
+    """
+
+    def __init__(self, A, stream=None, **params):
+        import torch
+        self._torch = torch
+        lib = load()
+        self._lib = lib
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if isinstance(A, torch.Tensor) and A.layout == torch.sparse_csr:
+            rp = A.crow_indices().to(device=dev, dtype=torch.int32).contiguous()
+            ci = A.col_indices().to(device=dev, dtype=torch.int32).contiguous()
+            v = A.values().to(device=dev, dtype=torch.float64).contiguous()
+            n = A.shape[0]
+        else:
+            rp = torch.as_tensor(np.asarray(A.row_ptr, dtype=np.int32)).to(dev)
+            ci = torch.as_tensor(np.asarray(A.col_idx, dtype=np.int32)).to(dev)
+            v = torch.as_tensor(np.asarray(A.val, dtype=np.float64)).to(dev)
+            n = int(A.n)
+        self.n = n
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        csr = amg_csr(n, int(ci.numel()), _ptr(rp), _ptr(ci), _ptr(v))
+        p = params_default(**params)
+        self.params = {f: getattr(p, f) for f in PARAM_FIELDS}
+        h = ctypes.c_void_p()
+        st = lib.amg_setup(ctypes.byref(csr), ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != OK:
+            raise AmgError(st, lib.amg_last_error(None).decode())
+        self._h = h
+        self.device = dev
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h:
+            self._lib.amg_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow=(OK,)):
+        if st not in allow:
+            raise AmgError(st, self._lib.amg_last_error(self._h).decode())
+        return st
+
+    # -- queries ------------------------------------------------------------
+    def info(self) -> dict:
+        inf = amg_info_t()
+        self._check(self._lib.amg_info(self._h, ctypes.byref(inf)))
+        L = inf.num_levels
+        return {"num_levels": L, "n": list(inf.n[:L]), "nnz": list(inf.nnz[:L]), "opc": inf.opc,
+                "num_pairwise": inf.num_pairwise, "setup_ms": inf.setup_ms, "vcycle_bytes": inf.vcycle_bytes,
+                "iteration_bytes": inf.iteration_bytes, "vcycle_launches": inf.vcycle_launches,
+                "iteration_launches": inf.iteration_launches, "precision": inf.precision}
+
+    @property
+    def num_levels(self) -> int:
+        return self.info()["num_levels"]
+
+    def aggregates(self, level: int) -> np.ndarray:
+        n = self.info()["n"][level]
+        out = np.zeros(n, np.int32)
+        self._check(self._lib.amg_get_aggregates(self._h, level, out.ctypes.data))
+        return out
+
+    def level_csr(self, level: int):
+        inf = self.info()
+        n, nnz = inf["n"][level], inf["nnz"][level]
+        rp, ci, v = np.zeros(n + 1, np.int32), np.zeros(nnz, np.int32), np.zeros(nnz, np.float64)
+        self._check(self._lib.amg_get_level_csr(self._h, level, rp.ctypes.data, ci.ctypes.data, v.ctypes.data))
+        return rp, ci, v
+
+    def l1(self, level: int) -> np.ndarray:
+        out = np.zeros(self.info()["n"][level], np.float64)
+        self._check(self._lib.amg_get_l1(self._h, level, out.ctypes.data))
+        return out
+
+    # -- solve phase --------------------------------------------------------
+    def _vec(self, x):
+        t = self._torch
+        return t.as_tensor(x, dtype=t.float64, device=self.device).contiguous()
+
+    def pcg_solve(self, b, x0=None, tol=1e-6, maxit=1000, precond=True):
+        """Alg. 1 on the GPU.  Returns dict(x, iters, hist, true_rel_res, status)."""
+        t = self._torch
+        b = self._vec(b)
+        x = t.zeros_like(b) if x0 is None else self._vec(x0).clone()
+        it = ctypes.c_int32(0)
+        tr = ctypes.c_double(0.0)
+        hist = np.zeros(maxit + 1)
+        fn = self._lib.amg_pcg_solve if precond else self._lib.amg_cg_solve
+        st = fn(self._h, _ptr(b), _ptr(x), tol, maxit, ctypes.byref(it), hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                ctypes.byref(tr))
+        self._check(st, allow=(OK, NOT_CONVERGED, ERR_BREAKDOWN))
+        return {"x": x, "iters": it.value, "hist": hist[: it.value + 1], "true_rel_res": tr.value, "status": st}
+
+    def solve_into(self, b, x, tol=1e-6, maxit=1000, precond=True):
+        """Alg. 1 on caller-owned device tensors (float64, contiguous); x: in u_0, out u."""
+        assert b.dtype == self._torch.float64 and x.dtype == self._torch.float64
+        it = ctypes.c_int32(0)
+        tr = ctypes.c_double(0.0)
+        fn = self._lib.amg_pcg_solve if precond else self._lib.amg_cg_solve
+        st = fn(self._h, _ptr(b), _ptr(x), tol, maxit, ctypes.byref(it), None, ctypes.byref(tr))
+        self._check(st, allow=(OK, NOT_CONVERGED, ERR_BREAKDOWN))
+        return {"iters": it.value, "true_rel_res": tr.value, "status": st}
+
+    def cg_solve(self, b, x0=None, tol=1e-6, maxit=1000):
+        return self.pcg_solve(b, x0, tol, maxit, precond=False)
+
+    def pcg_solve_host(self, b: np.ndarray, x: np.ndarray, tol=1e-6, maxit=1000, hist=None):
+        """Alg. 1 with host vectors (copies inside the call).  x is updated in place."""
+        assert b.dtype == np.float64 and x.dtype == np.float64 and b.flags.c_contiguous and x.flags.c_contiguous
+        it = ctypes.c_int32(0)
+        tr = ctypes.c_double(0.0)
+        hp = None if hist is None else hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        st = self._lib.amg_pcg_solve_host(self._h, b.ctypes.data, x.ctypes.data, tol, maxit, ctypes.byref(it), hp,
+                                          ctypes.byref(tr))
+        self._check(st, allow=(OK, NOT_CONVERGED, ERR_BREAKDOWN))
+        return {"iters": it.value, "true_rel_res": tr.value, "status": st}
+
+    def vcycle(self, r):
+        r = self._vec(r)
+        z = self._torch.empty_like(r)
+        self._check(self._lib.amg_vcycle(self._h, _ptr(r), _ptr(z)))
+        return z
+
+    def spmv(self, level, x):
+        x = self._vec(x)
+        y = self._torch.empty(self.info()["n"][level], dtype=self._torch.float64, device=self.device)
+        self._check(self._lib.amg_spmv(self._h, level, _ptr(x), _ptr(y)))
+        return y
+
+    # -- measurement --------------------------------------------------------
+    def time_vcycle(self, reps=20) -> float:
+        ms = ctypes.c_double(0.0)
+        self._check(self._lib.amg_time_vcycle(self._h, reps, ctypes.byref(ms)))
+        return ms.value
+
+    def time_kernel(self, which, level=0, reps=20) -> float:
+        ms = ctypes.c_double(0.0)
+        self._check(self._lib.amg_time_kernel(self._h, which, level, reps, ctypes.byref(ms)))
+        return ms.value
+
+    def kernel_bytes(self, which, level=0) -> float:
+        b = ctypes.c_double(0.0)
+        self._check(self._lib.amg_kernel_bytes(self._h, which, level, ctypes.byref(b)))
+        return b.value

@@ -1,0 +1,230 @@
+// Internal declarations of libamg (GB300, sm_103a).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "amg.h"
+
+#define AMG_MAXL 40
+#define AMG_BLOCK 256
+
+using bf16 = __nv_bfloat16;
+
+// ---------------------------------------------------------------------------
+// device buffers: every allocation is rounded up and padded by 256 bytes so
+// that vector loads that run past the logical end stay inside the allocation
+
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+enum { ST_TIMEOUT = 1, ST_BADPTR = 2, ST_BADCOL = 4, ST_NODIAG = 8, ST_NOTPOS = 16, ST_NAN = 32,
+       ST_ASYM = 64 };
+
+// FCG state kept on the device (Alg. 1 scalars and the stop logic)
+struct FcgState {
+  int it;         // number of updates of u so far
+  int done;       // 1: stop launching work (every solve-phase kernel checks it)
+  int status;     // amg_status of the solve
+  int need_true;  // 1: the next check kernel recomputes r = b - A u
+  int maxit;
+  int mixed;      // low-precision hierarchy: periodic true residual
+  int true_every;
+  int precflag;   // 0: B = I (plain CG)
+  int timing;     // 1: kernels timed in isolation; no stop bookkeeping, no history writes
+  int hist_len;   // entries of hist (maxit + 1)
+  double* hist;   // residual history (read through the state so that captured graphs stay valid)
+  double tol;
+  double nb;      // |b|_2
+  double res;     // current |r|/|b|
+  double true_res;
+  double rho;     // rho_{i-1}
+  double a;       // alpha_i / rho_i
+  double g;       // gamma_i / rho_{i-1}
+};
+
+struct Level {
+  int n = 0;
+  int64_t nnz = 0;
+  int G = 8;                 // lanes per row in the row kernels
+  int32_t* rp = nullptr;     // CSR (FP64 values)
+  int32_t* ci = nullptr;
+  double* v = nullptr;
+  float* vf = nullptr;       // low-precision copies of the values
+  bf16* vb = nullptr;
+  double* l1 = nullptr;      // sum_j |a_ij|
+  double* omega = nullptr;   // per-row damping (nullptr: 1)
+  double* dinv = nullptr;    // omega / l1
+  float* dinvf = nullptr;
+  int32_t* agg = nullptr;    // row -> row of the next level
+  int32_t* mptr = nullptr;   // members of each next-level row (ascending)
+  int32_t* mem = nullptr;
+  bool lowp = false;         // this level runs in float inside the V-cycle
+  // work vectors (double or float according to lowp)
+  void* r = nullptr;         // level input (restricted residual), levels > 0
+  void* za = nullptr;
+  void* zb = nullptr;
+  void* t = nullptr;         // residual
+  float* r0f = nullptr;      // level 0 low precision: float copy of the FCG residual
+};
+
+struct amg_handle {
+  amg_params p{};
+  cudaStream_t stream = nullptr;  // caller's stream
+  cudaStream_t cap = nullptr;     // internal stream used for graph capture
+  int nl = 0;
+  Level L[AMG_MAXL];
+  int npair = 0;
+  double setup_ms = 0.0;
+  // FCG vectors
+  double *b = nullptr, *u = nullptr, *r = nullptr, *w = nullptr, *d = nullptr, *v = nullptr,
+         *q = nullptr;
+  double* partial = nullptr;   // per-block partial sums of the reductions
+  unsigned* counter = nullptr; // last-block ticket
+  FcgState* st = nullptr;      // device state
+  FcgState* st_host = nullptr; // pinned host mirror
+  double* hist = nullptr;      // device residual history
+  int hist_cap = 0;
+  int* dev_flags = nullptr;    // error bits written by kernels
+  int* zero_flag = nullptr;    // a device int that stays 0 (skip flag of standalone V-cycles)
+  int red_grid = 0;
+  cudaGraphExec_t g_vcycle = nullptr;
+  cudaGraphExec_t g_iter = nullptr;
+  cudaGraphExec_t g_iter_cg = nullptr;
+  int launches_vcycle = 0;
+  int launches_iter = 0;
+  double bytes_vcycle = 0.0;   // algorithmic bytes of one V-cycle
+  double bytes_iter = 0.0;     // algorithmic bytes of one FCG iteration
+  std::string err;
+  std::vector<DBuf> bufs;
+};
+
+// ---------------------------------------------------------------------------
+// helpers shared by the translation units of the library
+
+amg_status amg_fail(amg_handle* h, amg_status s, const char* fmt, ...);
+void* amg_alloc(amg_handle* h, size_t bytes);  // zeroed, padded; nullptr on failure
+void amg_free_all(amg_handle* h);
+void amg_release(amg_handle* h, void* p);     // frees one allocation of the handle
+
+#define AMG_CK(h, call)                                                                     \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return amg_fail((h), AMG_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
+  } while (0)
+
+#define AMG_ALLOC(h, ptr, type, count)                                                      \
+  do {                                                                                      \
+    (ptr) = (type*)amg_alloc((h), sizeof(type) * (size_t)(count));                          \
+    if (!(ptr)) return amg_fail((h), AMG_ERR_OOM, "device allocation of %zu bytes failed",  \
+                                sizeof(type) * (size_t)(count));                           \
+  } while (0)
+
+static inline int amg_blocks(int64_t threads) { return (int)((threads + AMG_BLOCK - 1) / AMG_BLOCK); }
+
+// lanes per row: smallest power of two >= the average row length, in [2, 32]
+static inline int amg_lanes_for(int64_t nnz, int n) {
+  double avg = n ? (double)nnz / n : 1.0;
+  int G = 2;
+  while (G < 32 && G < avg) G *= 2;
+  return G;
+}
+
+void amg_set_setup_error(const std::string& msg);  // message for amg_last_error(NULL)
+amg_status amg_level_diag(amg_handle* h, int k);   // l1 norms and D = omega / l1 of level k
+
+// solve-phase internals (solve.cu)
+amg_status amg_prepare_solve(amg_handle* h);
+amg_status amg_capture_graphs(amg_handle* h);
+
+// ---------------------------------------------------------------------------
+// device-side helpers
+
+__device__ __forceinline__ double to_acc(double x) { return x; }
+__device__ __forceinline__ float to_acc(float x) { return x; }
+__device__ __forceinline__ float to_acc(bf16 x) { return __bfloat162float(x); }
+
+template <typename T>
+struct AccOf { using type = float; };
+template <>
+struct AccOf<double> { using type = double; };
+
+// mask of the G-lane group that contains this lane (G divides 32)
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+  if (G == 32) return 0xffffffffu;
+  unsigned lane = threadIdx.x & 31u;
+  return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+}
+
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T s) {
+  const unsigned m = group_mask<G>();
+#pragma unroll
+  for (int off = G / 2; off > 0; off >>= 1) s += __shfl_xor_sync(m, s, off);
+  return s;
+}
+
+// Deterministic block reduction of NV doubles: every thread passes its values;
+// on return thread 0 holds the block totals.  All threads of the block must
+// call it.  sm must hold 32*NV doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sm[k * 32 + warp] = v[k];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double x = lane < nw ? sm[k * 32 + lane] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+      v[k] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// Grid-wide deterministic reduction with the last-block pattern (no waiting):
+// each block stores its totals, takes a ticket; the block that takes the last
+// ticket sums all partials in a fixed order and returns true with the grid
+// totals in v (thread 0).  The counter is reset for the next kernel.
+template <int NV>
+__device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partial, unsigned* counter, double* sm) {
+  __shared__ bool is_last;
+  block_sum<NV>(v, sm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partial[(size_t)blockIdx.x * NV + k] = v[k];
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      x += __ldcg(&partial[(size_t)b * NV + k]);
+    v[k] = x;
+  }
+  block_sum<NV>(v, sm);
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}

@@ -1,0 +1,886 @@
+// Solve phase on the GPU: the V-cycle of Alg. 2 (read through the operator
+// B^k of Sec. 3.1) with l1-Jacobi smoothing, and the flexible PCG of Alg. 1.
+//
+// All kernels are HBM-bound.  Row kernels give each CSR row a group of G lanes
+// (G = power of two >= the average row length), so a warp reads a contiguous
+// run of values and column indices; the group sums with shuffles and its first
+// lane finishes the row (sweep update, residual, or the fused dot products).
+// Every solve-phase kernel takes a `skip` flag and returns at once when it is
+// set: the FCG iteration is replayed as a CUDA graph in batches and the
+// iterations after convergence cost one flag read per kernel.
+#include <algorithm>
+#include <cstring>
+
+#include "amg_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// V-cycle kernels (templates over the matrix value type MT, the vector type VT
+// of the level, and the output type OT)
+
+// first sweep from z = 0: z = D r (the level input may be FP64 and the level
+// float: then the rounded input is also kept in rcopy for the later sweeps)
+template <typename RT, typename VT>
+__global__ void __launch_bounds__(AMG_BLOCK) k_first(int n, const VT* __restrict__ dinv, const RT* __restrict__ r,
+                                                     VT* __restrict__ rcopy, VT* __restrict__ z, const int* skip) {
+  if (*skip) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  VT ri = (VT)r[i];
+  if (rcopy) rcopy[i] = ri;
+  z[i] = dinv[i] * ri;
+}
+
+// z_out = z + D (r - A z)
+template <int G, typename MT, typename VT, typename OT>
+__global__ void __launch_bounds__(AMG_BLOCK) k_sweep(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                     const MT* __restrict__ v, const VT* __restrict__ dinv,
+                                                     const VT* __restrict__ r, const VT* __restrict__ z,
+                                                     OT* __restrict__ zout, const int* skip) {
+  if (*skip) return;
+  using AT = VT;
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int row = (int)(t / G), lane = (int)(t % G);
+  if (row >= n) return;
+  int p0 = __ldg(&rp[row]), p1 = __ldg(&rp[row + 1]);
+  AT s = 0;
+  for (int p = p0 + lane; p < p1; p += G) s += (AT)to_acc(__ldg(&v[p])) * __ldg(&z[__ldg(&ci[p])]);
+  s = group_sum<G>(s);
+  if (lane == 0) zout[row] = (OT)(z[row] + dinv[row] * (r[row] - s));
+}
+
+// t = r - A z
+template <int G, typename MT, typename VT>
+__global__ void __launch_bounds__(AMG_BLOCK) k_resid(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                     const MT* __restrict__ v, const VT* __restrict__ r,
+                                                     const VT* __restrict__ z, VT* __restrict__ tout, const int* skip) {
+  if (*skip) return;
+  using AT = VT;
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int row = (int)(t / G), lane = (int)(t % G);
+  if (row >= n) return;
+  int p0 = __ldg(&rp[row]), p1 = __ldg(&rp[row + 1]);
+  AT s = 0;
+  for (int p = p0 + lane; p < p1; p += G) s += (AT)to_acc(__ldg(&v[p])) * __ldg(&z[__ldg(&ci[p])]);
+  s = group_sum<G>(s);
+  if (lane == 0) tout[row] = r[row] - s;
+}
+
+// r_c[J] = sum over the members i of aggregate J (ascending) of t_i
+template <typename VT, typename CT>
+__global__ void __launch_bounds__(AMG_BLOCK) k_restrict(int nc, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
+                                                        const VT* __restrict__ t, CT* __restrict__ rc, const int* skip) {
+  if (*skip) return;
+  int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= nc) return;
+  VT s = 0;
+  for (int m = mptr[J]; m < mptr[J + 1]; ++m) s += t[mem[m]];
+  rc[J] = (CT)s;
+}
+
+// z_i += z_c[agg(i)]  (unit piecewise-constant prolongator)
+template <typename VT, typename CT>
+__global__ void __launch_bounds__(AMG_BLOCK) k_prolong(int n, const int32_t* __restrict__ agg, const CT* __restrict__ zc,
+                                                       VT* __restrict__ z, const int* skip) {
+  if (*skip) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  z[i] += (VT)zc[agg[i]];
+}
+
+template <typename VT, typename OT>
+__global__ void k_copy(int n, const VT* __restrict__ a, OT* __restrict__ b, const int* skip) {
+  if (*skip) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (OT)a[i];
+}
+
+template <typename VT>
+__global__ void k_zero(int n, VT* __restrict__ a, const int* skip) {
+  if (*skip) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = (VT)0;
+}
+
+// plain y = A x (FP64), for the public amg_spmv
+template <int G>
+__global__ void __launch_bounds__(AMG_BLOCK) k_spmv(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                    const double* __restrict__ v, const double* __restrict__ x,
+                                                    double* __restrict__ y) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int row = (int)(t / G), lane = (int)(t % G);
+  if (row >= n) return;
+  double s = 0.0;
+  for (int p = rp[row] + lane; p < rp[row + 1]; p += G) s += v[p] * x[ci[p]];
+  s = group_sum<G>(s);
+  if (lane == 0) y[row] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 1 kernels (FP64).  Persistent grids of red_grid blocks; the scalar work
+// of each step is done by the last block of the grid-wide reduction.
+
+// r = b - A u;  |r|^2, |b|^2;  iteration 0 bookkeeping
+template <int G>
+__global__ void __launch_bounds__(AMG_BLOCK) k_fcg_init(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                        const double* __restrict__ v, const double* __restrict__ b,
+                                                        const double* __restrict__ u, double* __restrict__ r,
+                                                        FcgState* st, double* partial, unsigned* counter) {
+  __shared__ double sm[64];
+  double acc[2] = {0.0, 0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * G; t += stride) {
+    int row = (int)(t / G), lane = (int)(t % G);
+    double s = 0.0;
+    for (int p = rp[row] + lane; p < rp[row + 1]; p += G) s += v[p] * u[ci[p]];
+    s = group_sum<G>(s);
+    if (lane == 0) {
+      double bi = b[row], ri = bi - s;
+      r[row] = ri;
+      acc[0] += ri * ri;
+      acc[1] += bi * bi;
+    }
+  }
+  if (grid_sum<2>(acc, partial, counter, sm) && threadIdx.x == 0) {
+    double nb = sqrt(acc[1]);
+    st->nb = nb;
+    st->it = 0;
+    st->need_true = 0;
+    st->status = AMG_OK;
+    st->rho = 0.0;
+    if (nb == 0.0) {
+      st->res = 0.0;
+      st->true_res = 0.0;
+      if (st->hist_len > 0) st->hist[0] = 0.0;
+      st->done = 1;
+    } else {
+      double res = sqrt(acc[0]) / nb;
+      st->res = res;
+      if (st->hist_len > 0) st->hist[0] = res;
+      st->true_res = res;
+      st->done = (res < st->tol) || (st->maxit <= 0);
+      if (!(res < st->tol) && st->maxit <= 0) st->status = AMG_NOT_CONVERGED;
+    }
+  }
+}
+
+// v = A w;  alpha = w.r, beta = w.v, gamma = w.q;  rho and the step scalars
+template <int G>
+__global__ void __launch_bounds__(AMG_BLOCK) k_fcg_spmv_dots(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                             const double* __restrict__ v, const double* __restrict__ w,
+                                                             const double* __restrict__ r, const double* __restrict__ q,
+                                                             double* __restrict__ vout, FcgState* st, double* partial,
+                                                             unsigned* counter) {
+  if (st->done) return;
+  __shared__ double sm[96];
+  const bool first = st->it == 0;
+  double acc[3] = {0.0, 0.0, 0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * G; t += stride) {
+    int row = (int)(t / G), lane = (int)(t % G);
+    double s = 0.0;
+    for (int p = rp[row] + lane; p < rp[row + 1]; p += G) s += v[p] * w[ci[p]];
+    s = group_sum<G>(s);
+    if (lane == 0) {
+      double wi = w[row];
+      vout[row] = s;
+      acc[0] += wi * r[row];
+      acc[1] += wi * s;
+      if (!first) acc[2] += wi * q[row];
+    }
+  }
+  if (grid_sum<3>(acc, partial, counter, sm) && threadIdx.x == 0) {
+    if (st->timing) return;
+    double alpha = acc[0], beta = acc[1], gamma = acc[2];
+    double rho_new, g;
+    if (first) {
+      rho_new = beta;
+      g = 0.0;
+    } else {
+      rho_new = beta - gamma * gamma / st->rho;
+      g = gamma / st->rho;
+    }
+    if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+      st->status = AMG_ERR_BREAKDOWN;
+      st->done = 1;
+    } else {
+      st->g = g;
+      st->a = alpha / rho_new;
+      st->rho = rho_new;
+    }
+  }
+}
+
+// d = w - g d; q = v - g q; u += a d; r -= a q; |r|^2; stop bookkeeping
+__global__ void __launch_bounds__(AMG_BLOCK) k_fcg_axpy(int n, const double* __restrict__ w, const double* __restrict__ vv,
+                                                        double* __restrict__ d, double* __restrict__ q,
+                                                        double* __restrict__ u, double* __restrict__ r, FcgState* st,
+                                                        double* partial, unsigned* counter) {
+  if (st->done) return;
+  __shared__ double sm[32];
+  const bool first = st->it == 0;
+  const double g = st->g, a = st->a;
+  double acc[1] = {0.0};
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double di, qi;
+    if (first) {
+      di = w[i];
+      qi = vv[i];
+    } else {
+      di = w[i] - g * d[i];
+      qi = vv[i] - g * q[i];
+    }
+    d[i] = di;
+    q[i] = qi;
+    u[i] += a * di;
+    double ri = r[i] - a * qi;
+    r[i] = ri;
+    acc[0] += ri * ri;
+  }
+  if (grid_sum<1>(acc, partial, counter, sm) && threadIdx.x == 0) {
+    if (st->timing) return;
+    int it = st->it + 1;
+    st->it = it;
+    double res = sqrt(acc[0]) / st->nb;
+    st->res = res;
+    if (it < st->hist_len) st->hist[it] = res;
+    bool periodic = st->mixed && st->true_every > 0 && (it % st->true_every) == 0;
+    st->need_true = (res < st->tol) ? 1 : (periodic ? 2 : 0);
+    if (!st->need_true && it >= st->maxit) {
+      st->status = AMG_NOT_CONVERGED;
+      st->done = 1;
+    }
+  }
+}
+
+// true residual r = b - A u when the recursive residual dropped below tol
+// (need_true = 1) or periodically in mixed precision (need_true = 2)
+template <int G>
+__global__ void __launch_bounds__(AMG_BLOCK) k_fcg_true(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                        const double* __restrict__ v, const double* __restrict__ b,
+                                                        const double* __restrict__ u, double* __restrict__ r,
+                                                        FcgState* st, double* partial, unsigned* counter) {
+  if (st->done || !st->need_true) return;
+  __shared__ double sm[32];
+  double acc[1] = {0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * G; t += stride) {
+    int row = (int)(t / G), lane = (int)(t % G);
+    double s = 0.0;
+    for (int p = rp[row] + lane; p < rp[row + 1]; p += G) s += v[p] * u[ci[p]];
+    s = group_sum<G>(s);
+    if (lane == 0) {
+      double ri = b[row] - s;
+      r[row] = ri;
+      acc[0] += ri * ri;
+    }
+  }
+  if (grid_sum<1>(acc, partial, counter, sm) && threadIdx.x == 0) {
+    double tr = sqrt(acc[0]) / st->nb;
+    int it = st->it;
+    st->true_res = tr;
+    if (tr < st->tol) {
+      if (st->need_true == 2 && it < st->hist_len) st->hist[it] = tr;
+      st->res = tr;
+      st->status = AMG_OK;
+      st->done = 1;
+    } else {
+      if (it < st->hist_len) st->hist[it] = tr;
+      st->res = tr;
+      if (it >= st->maxit) {
+        st->status = AMG_NOT_CONVERGED;
+        st->done = 1;
+      }
+    }
+    st->need_true = 0;
+  }
+}
+
+// |b - A u| / |b| without touching r (exit report after breakdown / maxit)
+template <int G>
+__global__ void __launch_bounds__(AMG_BLOCK) k_true_norm(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                         const double* __restrict__ v, const double* __restrict__ b,
+                                                         const double* __restrict__ u, FcgState* st, double* partial,
+                                                         unsigned* counter) {
+  __shared__ double sm[32];
+  double acc[1] = {0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * G; t += stride) {
+    int row = (int)(t / G), lane = (int)(t % G);
+    double s = 0.0;
+    for (int p = rp[row] + lane; p < rp[row + 1]; p += G) s += v[p] * u[ci[p]];
+    s = group_sum<G>(s);
+    if (lane == 0) {
+      double ri = b[row] - s;
+      acc[0] += ri * ri;
+    }
+  }
+  if (grid_sum<1>(acc, partial, counter, sm) && threadIdx.x == 0) st->true_res = st->nb > 0 ? sqrt(acc[0]) / st->nb : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers (dispatch on the lanes per row)
+
+#define DISPATCH_G(G, CALL)            \
+  switch (G) {                         \
+    case 2: { constexpr int GG = 2; CALL; } break;   \
+    case 4: { constexpr int GG = 4; CALL; } break;   \
+    case 8: { constexpr int GG = 8; CALL; } break;   \
+    case 16: { constexpr int GG = 16; CALL; } break; \
+    default: { constexpr int GG = 32; CALL; } break; \
+  }
+
+template <typename MT, typename VT, typename OT>
+static void launch_sweep(cudaStream_t s, const Level& L, const MT* vals, const VT* dinv, const VT* r, const VT* z, OT* out,
+                         const int* skip) {
+  int nb = amg_blocks((int64_t)L.n * L.G);
+  DISPATCH_G(L.G, (k_sweep<GG, MT, VT, OT><<<nb, AMG_BLOCK, 0, s>>>(L.n, L.rp, L.ci, vals, dinv, r, z, out, skip)));
+}
+
+template <typename MT, typename VT>
+static void launch_resid(cudaStream_t s, const Level& L, const MT* vals, const VT* r, const VT* z, VT* t, const int* skip) {
+  int nb = amg_blocks((int64_t)L.n * L.G);
+  DISPATCH_G(L.G, (k_resid<GG, MT, VT><<<nb, AMG_BLOCK, 0, s>>>(L.n, L.rp, L.ci, vals, r, z, t, skip)));
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle recording.  Level k < nl-1 runs in VT (double, or float when the
+// hierarchy is low precision); the coarsest level always runs in FP64.
+
+struct VRec {
+  amg_handle* h;
+  cudaStream_t s;
+  const int* skip;
+  int launches = 0;
+  double bytes = 0.0;  // algorithmic bytes of the recorded launches
+  void add(double b) {
+    launches++;
+    bytes += b;
+  }
+};
+
+// algorithmic bytes: a row pass reads the row pointers, every value and column
+// index once, and (by cache reuse) the gathered vector once
+static double row_pass(const Level& L, double sv) { return (double)L.nnz * (sv + 4.0) + 4.0 * (L.n + 1.0); }
+static double val_bytes(const Level& L) { return L.lowp ? (L.vb ? 2.0 : 4.0) : 8.0; }
+static double vec_bytes(const Level& L) { return L.lowp ? 4.0 : 8.0; }
+
+// coarsest level: `sweeps` l1-Jacobi sweeps from zero on r (double); returns the
+// buffer that holds the result
+static double* rec_coarse(VRec& R, int k, const double* r, double* final_out) {
+  Level& L = R.h->L[k];
+  double* za = (double*)L.za;
+  double* zb = (double*)L.zb;
+  int sweeps = R.h->p.coarse_sweeps;
+  const double n = L.n;
+  double* cur = za;
+  if (sweeps <= 0) {
+    double* o = final_out ? final_out : za;
+    k_zero<double><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, o, R.skip);
+    R.add(8.0 * n);
+    return o;
+  }
+  double* o = (sweeps == 1 && final_out) ? final_out : za;
+  k_first<double, double><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, L.dinv, r, nullptr, o, R.skip);
+  R.add(24.0 * n);
+  cur = o;
+  for (int sw = 1; sw < sweeps; ++sw) {
+    double* nxt = (sw == sweeps - 1 && final_out) ? final_out : (cur == za ? zb : za);
+    launch_sweep<double, double, double>(R.s, L, L.v, L.dinv, r, cur, nxt, R.skip);
+    R.add(row_pass(L, 8.0) + 32.0 * n);
+    cur = nxt;
+  }
+  return cur;
+}
+
+// level k in type VT with matrix values MT.  rin: level input (RT = double at
+// level 0, VT elsewhere).  final_out (level 0 only): where the last sweep writes.
+template <typename VT, typename MT, typename RT>
+static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out);
+
+template <typename VT>
+static void rec_child(VRec& R, int k, const VT* t, VT* z) {
+  amg_handle* h = R.h;
+  Level& L = h->L[k];
+  Level& C = h->L[k + 1];
+  const int ncb = amg_blocks(C.n);
+  const double sx = sizeof(VT), n = L.n, nc = C.n;
+  if (k + 1 == h->nl - 1) {  // coarsest: FP64
+    k_restrict<VT, double><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, L.mptr, L.mem, t, (double*)C.r, R.skip);
+    R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 8.0 * nc);
+    double* zc = rec_coarse(R, k + 1, (const double*)C.r, nullptr);
+    k_prolong<VT, double><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, L.agg, zc, z, R.skip);
+    R.add(4.0 * n + 8.0 * nc + 2.0 * sx * n);
+  } else {
+    const double sc = vec_bytes(C);
+    k_restrict<VT, VT><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip);
+    R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc);
+    VT* zc;
+    if (C.lowp) zc = (VT*)rec_level<float, float, float>(R, k + 1, (const float*)C.r, nullptr);
+    else zc = (VT*)rec_level<double, double, double>(R, k + 1, (const double*)C.r, nullptr);
+    k_prolong<VT, VT><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, L.agg, zc, z, R.skip);
+    R.add(4.0 * n + sc * nc + 2.0 * sx * n);
+  }
+}
+
+template <typename VT, typename MT, typename RT>
+static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out) {
+  amg_handle* h = R.h;
+  Level& L = h->L[k];
+  const MT* vals;
+  if constexpr (std::is_same<MT, double>::value) vals = L.v;
+  else if constexpr (std::is_same<MT, float>::value) vals = L.vf;
+  else vals = L.vb;
+  const VT* dinv;
+  if constexpr (std::is_same<VT, double>::value) dinv = L.dinv;
+  else dinv = L.dinvf;
+  VT* za = (VT*)L.za;
+  VT* zb = (VT*)L.zb;
+  VT* t = (VT*)L.t;
+  const int nb = amg_blocks(L.n);
+  const double n = L.n, sx = sizeof(VT), sr = sizeof(RT), sv = sizeof(MT);
+  // the level's own copy of its input, in VT
+  const VT* r;
+  VT* rcopy = nullptr;
+  if constexpr (std::is_same<RT, VT>::value) {
+    r = rin;
+  } else {
+    rcopy = L.r0f ? (VT*)L.r0f : (VT*)L.r;
+    r = rcopy;
+  }
+  const double rc_bytes = rcopy ? sx * n : 0.0;
+  // pre-smoothing from zero
+  VT* cur = za;
+  if (h->p.pre_sweeps > 0) {
+    k_first<RT, VT><<<nb, AMG_BLOCK, 0, R.s>>>(L.n, dinv, rin, rcopy, za, R.skip);
+    R.add(sr * n + 2.0 * sx * n + rc_bytes);
+    for (int sw = 1; sw < h->p.pre_sweeps; ++sw) {
+      VT* nxt = cur == za ? zb : za;
+      launch_sweep<MT, VT, VT>(R.s, L, vals, dinv, r, cur, nxt, R.skip);
+      R.add(row_pass(L, sv) + 4.0 * sx * n);
+      cur = nxt;
+    }
+  } else {
+    if (rcopy) {
+      k_copy<RT, VT><<<nb, AMG_BLOCK, 0, R.s>>>(L.n, rin, rcopy, R.skip);
+      R.add(sr * n + rc_bytes);
+    }
+    k_zero<VT><<<nb, AMG_BLOCK, 0, R.s>>>(L.n, za, R.skip);
+    R.add(sx * n);
+  }
+  // residual, restriction, coarse correction, prolongation
+  launch_resid<MT, VT>(R.s, L, vals, r, cur, t, R.skip);
+  R.add(row_pass(L, sv) + 3.0 * sx * n);
+  rec_child<VT>(R, k, t, cur);
+  // post-smoothing
+  const int post = h->p.post_sweeps;
+  if (post == 0 && final_out) {
+    k_copy<VT, double><<<nb, AMG_BLOCK, 0, R.s>>>(L.n, cur, final_out, R.skip);
+    R.add(sx * n + 8.0 * n);
+    return nullptr;
+  }
+  for (int sw = 0; sw < post; ++sw) {
+    VT* nxt = cur == za ? zb : za;
+    if (sw == post - 1 && final_out) {
+      launch_sweep<MT, VT, double>(R.s, L, vals, dinv, r, cur, final_out, R.skip);
+      R.add(row_pass(L, sv) + 3.0 * sx * n + 8.0 * n);
+      return nullptr;
+    }
+    launch_sweep<MT, VT, VT>(R.s, L, vals, dinv, r, cur, nxt, R.skip);
+    R.add(row_pass(L, sv) + 4.0 * sx * n);
+    cur = nxt;
+  }
+  return cur;
+}
+
+// w = B r on the handle's FCG vectors
+static void record_vcycle(VRec& R, const double* r, double* w) {
+  amg_handle* h = R.h;
+  if (h->nl == 1) {
+    rec_coarse(R, 0, r, w);
+    return;
+  }
+  Level& L0 = h->L[0];
+  if (!L0.lowp) rec_level<double, double, double>(R, 0, r, w);
+  else if (L0.vb) rec_level<float, bf16, double>(R, 0, r, w);
+  else rec_level<float, float, double>(R, 0, r, w);
+}
+
+// algorithmic bytes of the outer kernels: SpMV + dots reads A, gathers w,
+// writes v, reads r and q; the axpys read w v d q u r and write d q u r
+static double bytes_spmv_dots(const Level& L) { return row_pass(L, 8.0) + 32.0 * L.n; }
+static double bytes_axpy(const Level& L) { return 80.0 * L.n; }
+
+static void record_iteration(VRec& R, bool precond) {
+  amg_handle* h = R.h;
+  Level& L = h->L[0];
+  const int g = h->red_grid;
+  FcgState* st = h->st;
+  const int* skip = &st->done;
+  R.skip = skip;
+  if (precond) record_vcycle(R, h->r, h->w);
+  else {
+    k_copy<double, double><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, h->r, h->w, skip);
+    R.add(16.0 * L.n);
+  }
+  DISPATCH_G(L.G, (k_fcg_spmv_dots<GG><<<g, AMG_BLOCK, 0, R.s>>>(L.n, L.rp, L.ci, L.v, h->w, h->r, h->q, h->v, st,
+                                                                 h->partial, h->counter)));
+  R.add(bytes_spmv_dots(L));
+  k_fcg_axpy<<<g, AMG_BLOCK, 0, R.s>>>(L.n, h->w, h->v, h->d, h->q, h->u, h->r, st, h->partial, h->counter);
+  R.add(bytes_axpy(L));
+  // the true-residual check moves data only once per solve (at convergence)
+  DISPATCH_G(L.G, (k_fcg_true<GG><<<g, AMG_BLOCK, 0, R.s>>>(L.n, L.rp, L.ci, L.v, h->b, h->u, h->r, st,
+                                                            h->partial, h->counter)));
+  R.add(0.0);
+}
+
+extern "C" amg_status amg_kernel_bytes(const amg_handle* h, int32_t which, int32_t level, double* bytes) {
+  if (!h || !bytes || level < 0 || level >= h->nl) return AMG_ERR_INVALID_ARG;
+  const Level& L = h->L[level];
+  const double n = L.n, sx = vec_bytes(L), sv = val_bytes(L);
+  const bool last = level == h->nl - 1;
+  switch (which) {
+    case 0: *bytes = row_pass(L, sv) + 4.0 * sx * n; return AMG_OK;
+    case 1: *bytes = row_pass(L, sv) + 3.0 * sx * n; return AMG_OK;
+    case 2:
+    case 3: {
+      if (last) return AMG_ERR_INVALID_ARG;
+      const Level& C = h->L[level + 1];
+      const double nc = C.n, sc = vec_bytes(C);
+      *bytes = which == 2 ? 4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc : 4.0 * n + sc * nc + 2.0 * sx * n;
+      return AMG_OK;
+    }
+    case 4: *bytes = level == 0 ? bytes_spmv_dots(L) : 0.0; return level == 0 ? AMG_OK : AMG_ERR_INVALID_ARG;
+    case 5: *bytes = level == 0 ? bytes_axpy(L) : 0.0; return level == 0 ? AMG_OK : AMG_ERR_INVALID_ARG;
+    default: return AMG_ERR_INVALID_ARG;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// preparation: work vectors, FCG state, graphs
+
+amg_status amg_prepare_solve(amg_handle* h) {
+  const int n = h->L[0].n;
+  for (int k = 0; k < h->nl; ++k) {
+    Level& L = h->L[k];
+    size_t es = L.lowp ? sizeof(float) : sizeof(double);
+    if (!(L.za = amg_alloc(h, es * L.n)) || !(L.zb = amg_alloc(h, es * L.n)) || !(L.t = amg_alloc(h, es * L.n)))
+      return amg_fail(h, AMG_ERR_OOM, "work vectors of level %d", k);
+    if (k > 0 && !(L.r = amg_alloc(h, es * L.n))) return amg_fail(h, AMG_ERR_OOM, "level input %d", k);
+    if (k == 0 && L.lowp) AMG_ALLOC(h, L.r0f, float, L.n);
+  }
+  AMG_ALLOC(h, h->b, double, n);
+  AMG_ALLOC(h, h->u, double, n);
+  AMG_ALLOC(h, h->r, double, n);
+  AMG_ALLOC(h, h->w, double, n);
+  AMG_ALLOC(h, h->d, double, n);
+  AMG_ALLOC(h, h->v, double, n);
+  AMG_ALLOC(h, h->q, double, n);
+  int dev = 0, sms = 148;
+  AMG_CK(h, cudaGetDevice(&dev));
+  AMG_CK(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int64_t want = amg_blocks((int64_t)n * h->L[0].G);
+  h->red_grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 4));
+  AMG_ALLOC(h, h->partial, double, (size_t)h->red_grid * 4);
+  AMG_ALLOC(h, h->counter, unsigned, 4);
+  AMG_ALLOC(h, h->st, FcgState, 1);
+  AMG_CK(h, cudaMallocHost((void**)&h->st_host, sizeof(FcgState)));
+  memset(h->st_host, 0, sizeof(FcgState));
+  h->hist_cap = 0;
+  AMG_CK(h, cudaStreamSynchronize(h->stream));
+  return amg_capture_graphs(h);
+}
+
+static void destroy_graphs(amg_handle* h) {
+  if (h->g_vcycle) cudaGraphExecDestroy(h->g_vcycle);
+  if (h->g_iter) cudaGraphExecDestroy(h->g_iter);
+  if (h->g_iter_cg) cudaGraphExecDestroy(h->g_iter_cg);
+  h->g_vcycle = h->g_iter = h->g_iter_cg = nullptr;
+}
+
+amg_status amg_capture_graphs(amg_handle* h) {
+  destroy_graphs(h);
+  // the graphs are captured even when use_graph = 0: the capture also counts
+  // the launches and the algorithmic bytes of a V-cycle and of an iteration
+  if (!h->cap) AMG_CK(h, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  auto capture = [&](auto&& body, cudaGraphExec_t* out, int* launches, double* bytes) -> amg_status {
+    cudaGraph_t g = nullptr;
+    AMG_CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    VRec R{h, h->cap, h->zero_flag};
+    body(R);
+    cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+    if (e != cudaSuccess) return amg_fail(h, AMG_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return amg_fail(h, AMG_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    if (launches) *launches = R.launches;
+    if (bytes) *bytes = R.bytes;
+    return AMG_OK;
+  };
+  amg_status st = capture([&](VRec& R) { record_vcycle(R, h->r, h->w); }, &h->g_vcycle, &h->launches_vcycle,
+                          &h->bytes_vcycle);
+  if (st != AMG_OK) return st;
+  st = capture([&](VRec& R) { record_iteration(R, true); }, &h->g_iter, &h->launches_iter, &h->bytes_iter);
+  if (st != AMG_OK) return st;
+  st = capture([&](VRec& R) { record_iteration(R, false); }, &h->g_iter_cg, nullptr, nullptr);
+  if (st != AMG_OK) return st;
+  AMG_CK(h, cudaGetLastError());
+  return AMG_OK;
+}
+
+void amg_release_graphs(amg_handle* h) {
+  destroy_graphs(h);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  h->cap = nullptr;
+  if (h->st_host) cudaFreeHost(h->st_host);
+  h->st_host = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// solves
+
+static amg_status ensure_hist(amg_handle* h, int maxit) {
+  if (maxit + 1 <= h->hist_cap) return AMG_OK;
+  if (h->hist) amg_release(h, h->hist);
+  AMG_ALLOC(h, h->hist, double, (size_t)maxit + 1);
+  h->hist_cap = maxit + 1;
+  return AMG_OK;
+}
+
+static amg_status run_fcg(amg_handle* h, bool precond, double tol, int maxit, int32_t* iters, double* res_hist,
+                          double* true_rel_res) {
+  cudaStream_t s = h->stream;
+  Level& L = h->L[0];
+  const int n = L.n;
+  if (maxit < 0) return amg_fail(h, AMG_ERR_INVALID_ARG, "maxit must be >= 0");
+  if (!(tol >= 0.0)) return amg_fail(h, AMG_ERR_INVALID_ARG, "tol must be >= 0");
+  amg_status st = ensure_hist(h, maxit);
+  if (st != AMG_OK) return st;
+  FcgState* hs = h->st_host;
+  memset(hs, 0, sizeof(FcgState));
+  hs->maxit = maxit;
+  hs->tol = tol;
+  hs->mixed = (h->p.precision != AMG_FP64) && precond;
+  hs->true_every = h->p.true_res_every;
+  hs->precflag = precond ? 1 : 0;
+  hs->hist = h->hist;
+  hs->hist_len = maxit + 1;
+  AMG_CK(h, cudaMemcpyAsync(h->st, hs, sizeof(FcgState), cudaMemcpyHostToDevice, s));
+  const int g = h->red_grid;
+  DISPATCH_G(L.G, (k_fcg_init<GG><<<g, AMG_BLOCK, 0, s>>>(n, L.rp, L.ci, L.v, h->b, h->u, h->r, h->st,
+                                                          h->partial, h->counter)));
+  AMG_CK(h, cudaGetLastError());
+  AMG_CK(h, cudaMemcpyAsync(hs, h->st, sizeof(FcgState), cudaMemcpyDeviceToHost, s));
+  AMG_CK(h, cudaStreamSynchronize(s));
+  if (hs->nb == 0.0) AMG_CK(h, cudaMemsetAsync(h->u, 0, sizeof(double) * (size_t)n, s));
+  const int batch = std::max(1, h->p.graph_batch);
+  while (!hs->done) {
+    for (int j = 0; j < batch; ++j) {
+      if (h->p.use_graph) {
+        AMG_CK(h, cudaGraphLaunch(precond ? h->g_iter : h->g_iter_cg, s));
+      } else {
+        VRec R{h, s, &h->st->done};
+        record_iteration(R, precond);
+        AMG_CK(h, cudaGetLastError());
+      }
+    }
+    AMG_CK(h, cudaMemcpyAsync(hs, h->st, sizeof(FcgState), cudaMemcpyDeviceToHost, s));
+    AMG_CK(h, cudaStreamSynchronize(s));
+  }
+  if (hs->status != AMG_OK && hs->nb > 0.0) {
+    DISPATCH_G(L.G, (k_true_norm<GG><<<g, AMG_BLOCK, 0, s>>>(n, L.rp, L.ci, L.v, h->b, h->u, h->st, h->partial,
+                                                             h->counter)));
+    AMG_CK(h, cudaMemcpyAsync(hs, h->st, sizeof(FcgState), cudaMemcpyDeviceToHost, s));
+    AMG_CK(h, cudaStreamSynchronize(s));
+  }
+  if (iters) *iters = hs->it;
+  if (true_rel_res) *true_rel_res = hs->true_res;
+  if (res_hist) {
+    AMG_CK(h, cudaMemcpyAsync(res_hist, h->hist, sizeof(double) * (size_t)(hs->it + 1), cudaMemcpyDeviceToHost, s));
+    AMG_CK(h, cudaStreamSynchronize(s));
+  }
+  return (amg_status)hs->status;
+}
+
+static amg_status solve_common(amg_handle* h, bool precond, const double* b, double* x, bool host, double tol,
+                               int32_t maxit, int32_t* iters, double* res_hist, double* true_rel_res) {
+  if (!h) return AMG_ERR_INVALID_ARG;
+  if (!b || !x) return amg_fail(h, AMG_ERR_INVALID_ARG, "b and x must not be NULL");
+  const size_t bytes = sizeof(double) * (size_t)h->L[0].n;
+  cudaMemcpyKind in = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaMemcpyKind outk = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  AMG_CK(h, cudaMemcpyAsync(h->b, b, bytes, in, h->stream));
+  AMG_CK(h, cudaMemcpyAsync(h->u, x, bytes, in, h->stream));
+  amg_status st = run_fcg(h, precond, tol, maxit, iters, res_hist, true_rel_res);
+  if (st < 0 && st != AMG_ERR_BREAKDOWN) return st;
+  AMG_CK(h, cudaMemcpyAsync(x, h->u, bytes, outk, h->stream));
+  AMG_CK(h, cudaStreamSynchronize(h->stream));
+  return st;
+}
+
+extern "C" amg_status amg_pcg_solve(amg_handle* h, const double* b, double* x, double tol, int32_t maxit,
+                                    int32_t* iters, double* res_hist, double* true_rel_res) {
+  return solve_common(h, true, b, x, false, tol, maxit, iters, res_hist, true_rel_res);
+}
+
+extern "C" amg_status amg_pcg_solve_host(amg_handle* h, const double* b, double* x, double tol, int32_t maxit,
+                                         int32_t* iters, double* res_hist, double* true_rel_res) {
+  return solve_common(h, true, b, x, true, tol, maxit, iters, res_hist, true_rel_res);
+}
+
+extern "C" amg_status amg_cg_solve(amg_handle* h, const double* b, double* x, double tol, int32_t maxit,
+                                   int32_t* iters, double* res_hist, double* true_rel_res) {
+  return solve_common(h, false, b, x, false, tol, maxit, iters, res_hist, true_rel_res);
+}
+
+static amg_status vcycle_on_handle(amg_handle* h) {
+  if (h->p.use_graph) {
+    AMG_CK(h, cudaGraphLaunch(h->g_vcycle, h->stream));
+  } else {
+    VRec R{h, h->stream, h->zero_flag};
+    record_vcycle(R, h->r, h->w);
+  }
+  AMG_CK(h, cudaGetLastError());
+  return AMG_OK;
+}
+
+extern "C" amg_status amg_vcycle(amg_handle* h, const double* r, double* z) {
+  if (!h) return AMG_ERR_INVALID_ARG;
+  if (!r || !z) return amg_fail(h, AMG_ERR_INVALID_ARG, "r and z must not be NULL");
+  const size_t bytes = sizeof(double) * (size_t)h->L[0].n;
+  AMG_CK(h, cudaMemcpyAsync(h->r, r, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  amg_status st = vcycle_on_handle(h);
+  if (st != AMG_OK) return st;
+  AMG_CK(h, cudaMemcpyAsync(z, h->w, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  AMG_CK(h, cudaStreamSynchronize(h->stream));
+  return AMG_OK;
+}
+
+extern "C" amg_status amg_spmv(amg_handle* h, int32_t level, const double* x, double* y) {
+  if (!h) return AMG_ERR_INVALID_ARG;
+  if (level < 0 || level >= h->nl || !x || !y) return amg_fail(h, AMG_ERR_INVALID_ARG, "bad level or pointer");
+  Level& L = h->L[level];
+  int nb = amg_blocks((int64_t)L.n * L.G);
+  DISPATCH_G(L.G, (k_spmv<GG><<<nb, AMG_BLOCK, 0, h->stream>>>(L.n, L.rp, L.ci, L.v, x, y)));
+  AMG_CK(h, cudaGetLastError());
+  AMG_CK(h, cudaStreamSynchronize(h->stream));
+  return AMG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// measurement helpers
+
+extern "C" amg_status amg_time_vcycle(amg_handle* h, int32_t reps, double* ms) {
+  if (!h || !ms || reps <= 0) return AMG_ERR_INVALID_ARG;
+  cudaEvent_t e0, e1;
+  AMG_CK(h, cudaEventCreate(&e0));
+  AMG_CK(h, cudaEventCreate(&e1));
+  amg_status st = vcycle_on_handle(h);  // warm-up
+  if (st != AMG_OK) return st;
+  AMG_CK(h, cudaEventRecord(e0, h->stream));
+  for (int i = 0; i < reps; ++i) {
+    st = vcycle_on_handle(h);
+    if (st != AMG_OK) return st;
+  }
+  AMG_CK(h, cudaEventRecord(e1, h->stream));
+  AMG_CK(h, cudaEventSynchronize(e1));
+  float t = 0.f;
+  AMG_CK(h, cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = (double)t / reps;
+  return AMG_OK;
+}
+
+// launches one kernel of the solve phase on the level's own buffers
+static amg_status launch_one(amg_handle* h, int which, int k) {
+  Level& L = h->L[k];
+  cudaStream_t s = h->stream;
+  const int* skip = h->zero_flag;
+  const int g = h->red_grid;
+  const bool coarsest = (k == h->nl - 1);
+  switch (which) {
+    case 0:  // sweep
+    case 1:  // residual
+      if (!L.lowp) {
+        const double* r = k == 0 ? h->r : (const double*)L.r;
+        if (which == 0) launch_sweep<double, double, double>(s, L, L.v, L.dinv, r, (double*)L.za, (double*)L.zb, skip);
+        else launch_resid<double, double>(s, L, L.v, r, (double*)L.za, (double*)L.t, skip);
+      } else {
+        const float* r = k == 0 ? L.r0f : (const float*)L.r;
+        if (L.vb) {
+          if (which == 0) launch_sweep<bf16, float, float>(s, L, L.vb, L.dinvf, r, (float*)L.za, (float*)L.zb, skip);
+          else launch_resid<bf16, float>(s, L, L.vb, r, (float*)L.za, (float*)L.t, skip);
+        } else {
+          if (which == 0) launch_sweep<float, float, float>(s, L, L.vf, L.dinvf, r, (float*)L.za, (float*)L.zb, skip);
+          else launch_resid<float, float>(s, L, L.vf, r, (float*)L.za, (float*)L.t, skip);
+        }
+      }
+      break;
+    case 2:
+    case 3: {
+      if (coarsest) return amg_fail(h, AMG_ERR_INVALID_ARG, "no restriction/prolongation on the coarsest level");
+      Level& C = h->L[k + 1];
+      bool ccoarse = (k + 1 == h->nl - 1);
+      if (which == 2) {
+        if (!L.lowp) k_restrict<double, double><<<amg_blocks(C.n), AMG_BLOCK, 0, s>>>(C.n, L.mptr, L.mem, (double*)L.t, (double*)C.r, skip);
+        else if (ccoarse) k_restrict<float, double><<<amg_blocks(C.n), AMG_BLOCK, 0, s>>>(C.n, L.mptr, L.mem, (float*)L.t, (double*)C.r, skip);
+        else k_restrict<float, float><<<amg_blocks(C.n), AMG_BLOCK, 0, s>>>(C.n, L.mptr, L.mem, (float*)L.t, (float*)C.r, skip);
+      } else {
+        if (!L.lowp) k_prolong<double, double><<<amg_blocks(L.n), AMG_BLOCK, 0, s>>>(L.n, L.agg, (double*)C.za, (double*)L.za, skip);
+        else if (ccoarse) k_prolong<float, double><<<amg_blocks(L.n), AMG_BLOCK, 0, s>>>(L.n, L.agg, (double*)C.za, (float*)L.za, skip);
+        else k_prolong<float, float><<<amg_blocks(L.n), AMG_BLOCK, 0, s>>>(L.n, L.agg, (float*)C.za, (float*)L.za, skip);
+      }
+      break;
+    }
+    case 4:
+      if (k != 0) return amg_fail(h, AMG_ERR_INVALID_ARG, "outer kernels run on level 0");
+      DISPATCH_G(L.G, (k_fcg_spmv_dots<GG><<<g, AMG_BLOCK, 0, s>>>(L.n, L.rp, L.ci, L.v, h->w, h->r, h->q, h->v, h->st,
+                                                                   h->partial, h->counter)));
+      break;
+    case 5:
+      if (k != 0) return amg_fail(h, AMG_ERR_INVALID_ARG, "outer kernels run on level 0");
+      k_fcg_axpy<<<g, AMG_BLOCK, 0, s>>>(L.n, h->w, h->v, h->d, h->q, h->u, h->r, h->st, h->partial, h->counter);
+      break;
+    default:
+      return amg_fail(h, AMG_ERR_INVALID_ARG, "unknown kernel id %d", which);
+  }
+  AMG_CK(h, cudaGetLastError());
+  return AMG_OK;
+}
+
+extern "C" amg_status amg_time_kernel(amg_handle* h, int32_t which, int32_t level, int32_t reps, double* ms) {
+  if (!h || !ms || reps <= 0) return AMG_ERR_INVALID_ARG;
+  if (level < 0 || level >= h->nl) return amg_fail(h, AMG_ERR_INVALID_ARG, "bad level");
+  amg_status st = ensure_hist(h, 1);
+  if (st != AMG_OK) return st;
+  if (which >= 4) {  // the outer kernels need a live (not done) FCG state with it > 0
+    FcgState* hs = h->st_host;
+    memset(hs, 0, sizeof(FcgState));
+    hs->it = 1;
+    hs->timing = 1;
+    hs->maxit = 1 << 30;
+    hs->tol = 0.0;
+    hs->nb = 1.0;
+    hs->rho = 1.0;
+    AMG_CK(h, cudaMemcpyAsync(h->st, hs, sizeof(FcgState), cudaMemcpyHostToDevice, h->stream));
+  }
+  cudaEvent_t e0, e1;
+  AMG_CK(h, cudaEventCreate(&e0));
+  AMG_CK(h, cudaEventCreate(&e1));
+  st = launch_one(h, which, level);
+  if (st != AMG_OK) return st;
+  AMG_CK(h, cudaEventRecord(e0, h->stream));
+  for (int i = 0; i < reps; ++i) {
+    st = launch_one(h, which, level);
+    if (st != AMG_OK) return st;
+  }
+  AMG_CK(h, cudaEventRecord(e1, h->stream));
+  AMG_CK(h, cudaEventSynchronize(e1));
+  float t = 0.f;
+  AMG_CK(h, cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = (double)t / reps;
+  return AMG_OK;
+}

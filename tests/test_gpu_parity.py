@@ -1,0 +1,292 @@
+"""GPU library against the CPU oracle, element by element, through the C ABI.
+
+Tolerances (FP64 path): aggregates and integer structure bit-exact; coarse
+operators equal to 1e-12 relative (bitwise expected: both sides sum in the
+same canonical order); l1 norms bitwise; one V-cycle to 1e-12 relative; FCG
+iteration counts within 1; solutions at the same iteration count to 1e-9
+relative.  Low-precision hierarchies: V-cycle to 1e-5 (FP32) / 2e-2 (BF16
+finest level) relative against the oracle's FP64 V-cycle and 1e-4 against the
+oracle's own emulation of the same precision; iterations within 2 of the
+emulation; true FP64 residual below the tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2303_02352_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_02352_gb300 import build
+    build.build()
+    from paper_2303_02352_gb300 import amg
+    return amg.load()
+
+
+def G(A, **kw):
+    from paper_2303_02352_gb300 import amg
+    return amg.Hierarchy(A, **kw)
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+PROBLEMS = {
+    "poisson16": lambda: W.poisson7(16),
+    "poisson13": lambda: W.poisson7(13),          # odd size: irregular aggregates, ragged tails
+    "poisson32": lambda: W.poisson7(32),
+    "diff7_20": lambda: W.diffusion7(20, 2.0, 1001),
+    "diff27_12": lambda: W.diffusion27(12, 2.0, 3),
+    "laplace1d": lambda: W.laplace1d(3001),
+}
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_hierarchy_bit_exact(name):
+    A = PROBLEMS[name]()
+    g = G(A)
+    o = O.Hierarchy(A)
+    info = g.info()
+    assert info["num_levels"] == o.num_levels
+    assert info["num_pairwise"] == len(o.pairwise_sizes)
+    for k in range(o.num_levels):
+        assert info["n"][k] == o.level_n(k) and info["nnz"][k] == o.level_nnz(k)
+        grp, gci, gv = g.level_csr(k)
+        orp, oci, ov = o.level_csr(k)
+        assert np.array_equal(grp, orp) and np.array_equal(gci, oci)
+        assert np.max(np.abs(gv - ov)) <= 1e-12 * np.max(np.abs(ov))
+        assert np.array_equal(gv.view(np.uint64), ov.view(np.uint64))  # canonical order on both sides
+        assert np.array_equal(g.l1(k).view(np.uint64), o.level_l1(k).view(np.uint64))
+        if k < o.num_levels - 1:
+            assert np.array_equal(g.aggregates(k), o.level_agg(k))
+
+
+@pytest.mark.parametrize("name", ["poisson16", "poisson13", "diff7_20", "diff27_12", "laplace1d"])
+def test_vcycle_and_spmv_parity(name):
+    A = PROBLEMS[name]()
+    g, o = G(A), O.Hierarchy(A)
+    for seed in (1, 2):
+        r = W.random_vector(A.n, seed)
+        zg = g.vcycle(r).cpu().numpy()
+        zo = o.vcycle(r)
+        assert rel(zg, zo) < 1e-12
+    x = W.random_vector(A.n, 7)
+    for k in range(o.num_levels):
+        xk = x[: o.level_n(k)]
+        assert rel(g.spmv(k, xk).cpu().numpy(), o.spmv(k, xk)) < 1e-14
+
+
+@pytest.mark.parametrize("name", ["poisson16", "poisson13", "poisson32", "diff7_20", "diff27_12"])
+def test_fcg_parity(name):
+    A = PROBLEMS[name]()
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 1))
+    g, o = G(A), O.Hierarchy(A)
+    rg, ro = g.pcg_solve(b), o.fcg(b)
+    assert rg["status"] == 0 and ro["status"] == 0
+    assert abs(rg["iters"] - ro["iters"]) <= 1
+    assert rg["true_rel_res"] < 1e-6
+    # same iteration count -> same iterate
+    m = min(rg["iters"], ro["iters"])
+    xg = g.pcg_solve(b, tol=0.0, maxit=m)["x"].cpu().numpy()
+    xo = o.fcg(b, tol=0.0, maxit=m)["x"]
+    assert rel(xg, xo) < 1e-9
+    # residual history
+    hg = g.pcg_solve(b, tol=0.0, maxit=m)["hist"]
+    assert np.allclose(hg, o.fcg(b, tol=0.0, maxit=m)["hist"], rtol=1e-8, atol=0)
+
+
+def test_plain_cg_parity():
+    A = W.poisson7(12)
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 4))
+    g, o = G(A), O.Hierarchy(A)
+    rg = g.cg_solve(b, tol=1e-8)
+    ro = o.fcg(b, tol=1e-8, precflag=0)
+    assert abs(rg["iters"] - ro["iters"]) <= 1 and rg["true_rel_res"] < 1e-8
+    m = min(rg["iters"], ro["iters"])
+    xg = g.cg_solve(b, tol=0.0, maxit=m)["x"].cpu().numpy()
+    assert rel(xg, o.fcg(b, tol=0.0, maxit=m, precflag=0)["x"]) < 1e-9
+
+
+def test_determinism_bitwise():
+    A = W.diffusion27(10, 2.0, 5)
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 2))
+    g1, g2 = G(A), G(A)
+    for k in range(g1.num_levels - 1):
+        assert np.array_equal(g1.aggregates(k), g2.aggregates(k))
+    x1 = g1.pcg_solve(b)["x"].cpu().numpy()
+    x2 = g2.pcg_solve(b)["x"].cpu().numpy()
+    x3 = g1.pcg_solve(b)["x"].cpu().numpy()
+    assert np.array_equal(x1.view(np.uint64), x2.view(np.uint64))
+    assert np.array_equal(x1.view(np.uint64), x3.view(np.uint64))
+
+
+def test_graph_and_direct_launch_agree():
+    A = W.poisson7(14)
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 3))
+    xg = G(A).pcg_solve(b)["x"].cpu().numpy()
+    xd = G(A, use_graph=0).pcg_solve(b)["x"].cpu().numpy()
+    assert np.array_equal(xg.view(np.uint64), xd.view(np.uint64))
+    for batch in (1, 7):
+        xb = G(A, graph_batch=batch).pcg_solve(b)["x"].cpu().numpy()
+        assert np.array_equal(xg.view(np.uint64), xb.view(np.uint64))
+
+
+def test_host_entry_point_matches_device():
+    A = W.poisson7(15)
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 6))
+    g = G(A)
+    rd = g.pcg_solve(b)
+    x = np.zeros(A.n)
+    rh = g.pcg_solve_host(np.ascontiguousarray(b), x)
+    assert rh["iters"] == rd["iters"]
+    assert np.array_equal(x.view(np.uint64), rd["x"].cpu().numpy().view(np.uint64))
+
+
+# ---------------------------------------------------------------------------
+# edge and degenerate cases
+
+
+def test_single_level_problem():
+    A = W.poisson7(4)  # n = 64 <= 40 * 4: only the coarsest level (20 sweeps)
+    g, o = G(A), O.Hierarchy(A)
+    assert g.num_levels == 1 == o.num_levels
+    r = W.random_vector(A.n, 1)
+    assert rel(g.vcycle(r).cpu().numpy(), o.vcycle(r)) < 1e-13
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 2))
+    rg, ro = g.pcg_solve(b), o.fcg(b)
+    assert abs(rg["iters"] - ro["iters"]) <= 1
+
+
+def test_zero_rhs_maxit_and_initial_guess():
+    A = W.poisson7(10)
+    g = G(A)
+    r = g.pcg_solve(np.zeros(A.n))
+    assert r["iters"] == 0 and r["status"] == 0 and float(r["x"].abs().max()) == 0.0
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 2))
+    r = g.pcg_solve(b, tol=1e-14, maxit=3)
+    assert r["status"] == 1 and r["iters"] == 3 and len(r["hist"]) == 4
+    ro = O.Hierarchy(A).fcg(b, tol=1e-14, maxit=3)
+    assert rel(r["x"].cpu().numpy(), ro["x"]) < 1e-12
+    # an exact initial guess: converged at iteration 0
+    xs = np.linalg.solve(A.to_scipy().toarray(), b)
+    r = g.pcg_solve(b, x0=xs)
+    assert r["iters"] == 0 and r["status"] == 0
+
+
+def test_custom_parameters_match_oracle():
+    A = W.diffusion7(14, 1.0, 77)
+    kw = dict(aggr_steps=2, pre_sweeps=2, post_sweeps=3, coarse_sweeps=7, coarse_size=30)
+    g = G(A, **kw)
+    o = O.Hierarchy(A, **kw)
+    assert g.num_levels == o.num_levels
+    r = W.random_vector(A.n, 3)
+    assert rel(g.vcycle(r).cpu().numpy(), o.vcycle(r)) < 1e-12
+    kw0 = dict(pre_sweeps=0, post_sweeps=1, coarse_sweeps=1)
+    g0, o0 = G(A, **kw0), O.Hierarchy(A, **kw0)
+    assert rel(g0.vcycle(r).cpu().numpy(), o0.vcycle(r)) < 1e-12
+
+
+def _bad(A, **mut):
+    rp, ci, v = A.row_ptr.copy(), A.col_idx.copy(), A.val.copy()
+    if "asym" in mut:
+        v[1] += 1e-3
+    if "unsorted" in mut:
+        ci[0], ci[1] = ci[1], ci[0]
+    if "nodiag" in mut:
+        v = v.copy()
+        p = A.row_ptr[2]
+        ci[p] = ci[p]  # keep structure, break the diagonal below
+        # replace row 2's diagonal column by a neighbour already present -> duplicate columns
+        d = [q for q in range(A.row_ptr[2], A.row_ptr[3]) if ci[q] == 2][0]
+        ci[d] = ci[d - 1]
+    if "negdiag" in mut:
+        d = [q for q in range(A.row_ptr[0], A.row_ptr[1]) if ci[q] == 0][0]
+        v[d] = -1.0
+    if "nan" in mut:
+        v[5] = np.nan
+    if "range" in mut:
+        ci[3] = A.n + 5
+    return W.CSR(A.n, rp, ci, v)
+
+
+@pytest.mark.parametrize("kind,status", [("asym", -1), ("unsorted", -1), ("nodiag", -1), ("negdiag", -2),
+                                         ("nan", -1), ("range", -1)])
+def test_invalid_inputs_are_rejected(kind, status):
+    from paper_2303_02352_gb300 import amg
+    A = W.poisson7(5)
+    with pytest.raises(amg.AmgError) as e:
+        G(_bad(A, **{kind: True}))
+    assert e.value.status == status
+
+
+# ---------------------------------------------------------------------------
+# mixed precision
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("name", ["poisson16", "diff27_12", "diff7_20"])
+def test_low_precision_hierarchy(name, prec):
+    A = PROBLEMS[name]()
+    g = G(A, precision=prec)
+    o64 = O.Hierarchy(A)
+    olo = O.Hierarchy(A, precision=prec)
+    r = W.random_vector(A.n, 9)
+    zg = g.vcycle(r).cpu().numpy()
+    assert rel(zg, olo.vcycle(r)) < 1e-4
+    assert rel(zg, o64.vcycle(r)) < (1e-5 if prec == 1 else 2e-2)
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 1))
+    rg, rlo = g.pcg_solve(b), olo.fcg(b)
+    assert rg["status"] == 0 and rg["true_rel_res"] < 1e-6
+    assert abs(rg["iters"] - rlo["iters"]) <= 2
+
+
+# ---------------------------------------------------------------------------
+# full-size workload of the benchmark (7-point Poisson 160^3)
+
+
+@pytest.fixture(scope="module")
+def big():
+    A = W.poisson7(160)
+    return A, G(A), O.Hierarchy(A)
+
+
+def test_full_size_hierarchy_bit_exact(big):
+    A, g, o = big
+    sizes = [(4096000, 28518400), (512000, 3545600), (64000, 438400), (8000, 53600), (4000, 26400)]
+    info = g.info()
+    assert list(zip(info["n"], info["nnz"])) == sizes
+    assert [(o.level_n(k), o.level_nnz(k)) for k in range(o.num_levels)] == sizes
+    for k in range(o.num_levels - 1):
+        assert np.array_equal(g.aggregates(k), o.level_agg(k))
+    i = np.arange(A.n)
+    x, y, z = i % 160, (i // 160) % 160, i // 25600
+    assert np.array_equal(g.aggregates(0), x // 2 + 80 * (y // 2) + 6400 * (z // 2))
+    for k in range(1, o.num_levels):
+        _, _, gv = g.level_csr(k)
+        _, _, ov = o.level_csr(k)
+        assert np.array_equal(gv, ov)
+
+
+def test_full_size_vcycle_and_solve(big):
+    A, g, o = big
+    r = W.random_vector(A.n, 11)
+    assert rel(g.vcycle(r).cpu().numpy(), o.vcycle(r)) < 1e-12
+    xs = W.random_vector(A.n, 2)
+    b = W.rhs_from_solution(A, xs)
+    res = g.pcg_solve(b)
+    assert res["status"] == 0 and res["true_rel_res"] < 1e-6
+    x = res["x"].cpu().numpy()
+    rr = b - A.to_scipy() @ x
+    assert abs(np.linalg.norm(rr) / np.linalg.norm(b) - res["true_rel_res"]) < 1e-9
+    # the oracle's first two FCG iterates
+    xg = g.pcg_solve(b, tol=0.0, maxit=2)["x"].cpu().numpy()
+    assert rel(xg, o.fcg(b, tol=0.0, maxit=2)["x"]) < 1e-10
