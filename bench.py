@@ -284,11 +284,13 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     for _ in range(args.steps):
         res = solve()
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     dist.barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps

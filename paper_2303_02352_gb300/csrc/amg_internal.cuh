@@ -53,7 +53,9 @@ struct FcgState {
 struct Level {
   int n = 0;
   int64_t nnz = 0;
-  int G = 8;                 // lanes per row in the row kernels
+  int maxrow = 0;            // longest row (nonzeros)
+  int R = 256;               // tile height of the row kernels with this level's V-cycle value type
+  int Rd = 256;              // tile height with FP64 values (outer kernels, amg_spmv)
   int32_t* rp = nullptr;     // CSR (FP64 values)
   int32_t* ci = nullptr;
   double* v = nullptr;
@@ -94,7 +96,8 @@ struct amg_handle {
   int hist_cap = 0;
   int* dev_flags = nullptr;    // error bits written by kernels
   int* zero_flag = nullptr;    // a device int that stays 0 (skip flag of standalone V-cycles)
-  int red_grid = 0;
+  int red_grid = 0;            // persistent grid of the outer row kernels
+  int ax_grid = 0;             // grid of the fused axpys
   cudaGraphExec_t g_vcycle = nullptr;
   cudaGraphExec_t g_iter = nullptr;
   cudaGraphExec_t g_iter_cg = nullptr;
@@ -130,12 +133,13 @@ void amg_release(amg_handle* h, void* p);     // frees one allocation of the han
 
 static inline int amg_blocks(int64_t threads) { return (int)((threads + AMG_BLOCK - 1) / AMG_BLOCK); }
 
-// lanes per row: smallest power of two >= the average row length, in [2, 32]
-static inline int amg_lanes_for(int64_t nnz, int n) {
-  double avg = n ? (double)nnz / n : 1.0;
-  int G = 2;
-  while (G < 32 && G < avg) G *= 2;
-  return G;
+// tile height of the row kernels: the largest of 256, 128, 64, 32 rows whose
+// longest-row bound fits the shared-memory tile (24 KB of values + indices)
+static inline int amg_tile_rows(int maxrow, int value_bytes) {
+  const int cap = 24576 / (value_bytes + 4);
+  int R = 256;
+  while (R > 32 && (int64_t)R * maxrow > cap) R /= 2;
+  return R;
 }
 
 void amg_set_setup_error(const std::string& msg);  // message for amg_last_error(NULL)

@@ -455,6 +455,11 @@ __global__ void k_sort_members(int nc, const int32_t* __restrict__ mptr, int32_t
   }
 }
 
+__global__ void k_maxrow(int n, const int32_t* __restrict__ rp, int* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicMax(out, rp[i + 1] - rp[i]);
+}
+
 // l1-Jacobi: M_ii = sum_j |a_ij| (CSR order), D_i = omega_i / M_ii
 __global__ void k_l1(int n, const int32_t* __restrict__ rp, const double* __restrict__ v,
                      const double* __restrict__ omega, double* __restrict__ l1, double* __restrict__ dinv,
@@ -728,8 +733,16 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
   const bool lowp = h->p.precision != AMG_FP64 && h->nl > 1;
   for (int k = 0; k < h->nl; ++k) {
     Level& L = h->L[k];
-    L.G = amg_lanes_for(L.nnz, L.n);
     L.lowp = lowp && k < h->nl - 1;
+    AMG_CK(h, cudaMemsetAsync(h->dev_flags, 0, sizeof(int), s));
+    k_maxrow<<<amg_blocks(L.n), AMG_BLOCK, 0, s>>>(L.n, L.rp, h->dev_flags);
+    int mr = 0;
+    amg_status st0 = sync_read(h, h->dev_flags, &mr);
+    if (st0 != AMG_OK) return st0;
+    AMG_CK(h, cudaMemsetAsync(h->dev_flags, 0, sizeof(int), s));
+    L.maxrow = mr;
+    L.Rd = amg_tile_rows(mr, 8);
+    L.R = amg_tile_rows(mr, L.lowp ? ((h->p.precision == AMG_FP32_BF16FINE && k == 0) ? 2 : 4) : 8);
     AMG_ALLOC(h, L.l1, double, L.n);
     AMG_ALLOC(h, L.dinv, double, L.n);
     if (L.lowp) {

@@ -14,8 +14,64 @@
 #include "amg_internal.cuh"
 
 // ---------------------------------------------------------------------------
-// V-cycle kernels (templates over the matrix value type MT, the vector type VT
-// of the level, and the output type OT)
+// Row tiles.  A block owns R consecutive rows (R = the level's tile height).
+// The nonzeros of those rows, [rp[row0], rp[row0 + R]), are contiguous in CSR:
+// the block copies their values and column indices into shared memory with
+// 16-byte loads (every byte of A is read once, fully coalesced), then each
+// thread finishes one row from shared memory and gathers the vector through
+// L1/L2.  One thread per row keeps the floating-point work at one multiply-add
+// per nonzero (no shuffle reduction), which matters for FP64 on this part.
+// A tile whose nonzeros exceed the buffer reads A directly from global memory
+// (the tile height is chosen from the longest row, so this is a fallback only
+// for matrices with very long rows).
+
+#define TILE_BYTES 24576
+
+template <typename MT>
+struct TileSmem {
+  static constexpr int VE = 16 / (int)sizeof(MT);              // elements per 16 bytes
+  static constexpr int CAP = TILE_BYTES / ((int)sizeof(MT) + 4);  // nonzeros per tile
+  MT v[CAP + 2 * VE];
+  int32_t c[CAP + 8];
+};
+
+// s = sum_j a_ij x_j for row row0 + threadIdx.x (0 for threads past row1).
+// Ends with the tile's nonzeros in shared memory; the caller must
+// __syncthreads() before the next call on the same buffer.
+template <int R, typename MT, typename XT, typename AT>
+__device__ __forceinline__ AT tile_row_dot(TileSmem<MT>& sm, int row0, int row1, const int32_t* __restrict__ rp,
+                                           const int32_t* __restrict__ ci, const MT* __restrict__ v,
+                                           const XT* __restrict__ x) {
+  constexpr int VE = TileSmem<MT>::VE, CAP = TileSmem<MT>::CAP;
+  const int p0 = __ldg(&rp[row0]);
+  const int p1 = __ldg(&rp[row1]);
+  const int row = row0 + (int)threadIdx.x;
+  int q0 = 0, q1 = 0;
+  if (row < row1) {
+    q0 = __ldg(&rp[row]);
+    q1 = __ldg(&rp[row + 1]);
+  }
+  AT s = 0;
+  if (p1 - p0 <= CAP) {
+    const int a0 = p0 & ~(VE - 1);
+    const int nv = (p1 - a0 + VE - 1) / VE;
+    const uint4* gv = reinterpret_cast<const uint4*>(v + a0);
+    uint4* dv = reinterpret_cast<uint4*>(sm.v);
+    for (int k = threadIdx.x; k < nv; k += R) dv[k] = __ldg(gv + k);
+    const int c0 = p0 & ~3;
+    const int nc = (p1 - c0 + 3) >> 2;
+    const uint4* gc = reinterpret_cast<const uint4*>(ci + c0);
+    uint4* dc = reinterpret_cast<uint4*>(sm.c);
+    for (int k = threadIdx.x; k < nc; k += R) dc[k] = __ldg(gc + k);
+    __syncthreads();
+#pragma unroll 8
+    for (int q = q0; q < q1; ++q) s += (AT)to_acc(sm.v[q - a0]) * (AT)__ldg(&x[sm.c[q - c0]]);
+  } else {
+#pragma unroll 4
+    for (int q = q0; q < q1; ++q) s += (AT)to_acc(__ldg(&v[q])) * (AT)__ldg(&x[__ldg(&ci[q])]);
+  }
+  return s;
+}
 
 // first sweep from z = 0: z = D r (the level input may be FP64 and the level
 // float: then the rounded input is also kept in rcopy for the later sweeps)
@@ -30,39 +86,43 @@ __global__ void __launch_bounds__(AMG_BLOCK) k_first(int n, const VT* __restrict
   z[i] = dinv[i] * ri;
 }
 
-// z_out = z + D (r - A z)
-template <int G, typename MT, typename VT, typename OT>
-__global__ void __launch_bounds__(AMG_BLOCK) k_sweep(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                     const MT* __restrict__ v, const VT* __restrict__ dinv,
-                                                     const VT* __restrict__ r, const VT* __restrict__ z,
-                                                     OT* __restrict__ zout, const int* skip) {
+// l1-Jacobi sweep z_out = z + D (r - A z)
+template <int R, typename MT, typename VT, typename OT>
+__global__ void __launch_bounds__(R) k_sweep(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                             const MT* __restrict__ v, const VT* __restrict__ dinv,
+                                             const VT* __restrict__ r, const VT* __restrict__ z,
+                                             OT* __restrict__ zout, const int* skip) {
   if (*skip) return;
-  using AT = VT;
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int row = (int)(t / G), lane = (int)(t % G);
-  if (row >= n) return;
-  int p0 = __ldg(&rp[row]), p1 = __ldg(&rp[row + 1]);
-  AT s = 0;
-  for (int p = p0 + lane; p < p1; p += G) s += (AT)to_acc(__ldg(&v[p])) * __ldg(&z[__ldg(&ci[p])]);
-  s = group_sum<G>(s);
-  if (lane == 0) zout[row] = (OT)(z[row] + dinv[row] * (r[row] - s));
+  __shared__ __align__(16) TileSmem<MT> sm;
+  const int row0 = blockIdx.x * R, row1 = min(row0 + R, n);
+  const VT s = tile_row_dot<R, MT, VT, VT>(sm, row0, row1, rp, ci, v, z);
+  const int row = row0 + threadIdx.x;
+  if (row < row1) zout[row] = (OT)(z[row] + dinv[row] * (r[row] - s));
 }
 
-// t = r - A z
-template <int G, typename MT, typename VT>
-__global__ void __launch_bounds__(AMG_BLOCK) k_resid(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                     const MT* __restrict__ v, const VT* __restrict__ r,
-                                                     const VT* __restrict__ z, VT* __restrict__ tout, const int* skip) {
+// residual t = r - A z
+template <int R, typename MT, typename VT>
+__global__ void __launch_bounds__(R) k_resid(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                             const MT* __restrict__ v, const VT* __restrict__ r,
+                                             const VT* __restrict__ z, VT* __restrict__ tout, const int* skip) {
   if (*skip) return;
-  using AT = VT;
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int row = (int)(t / G), lane = (int)(t % G);
-  if (row >= n) return;
-  int p0 = __ldg(&rp[row]), p1 = __ldg(&rp[row + 1]);
-  AT s = 0;
-  for (int p = p0 + lane; p < p1; p += G) s += (AT)to_acc(__ldg(&v[p])) * __ldg(&z[__ldg(&ci[p])]);
-  s = group_sum<G>(s);
-  if (lane == 0) tout[row] = r[row] - s;
+  __shared__ __align__(16) TileSmem<MT> sm;
+  const int row0 = blockIdx.x * R, row1 = min(row0 + R, n);
+  const VT s = tile_row_dot<R, MT, VT, VT>(sm, row0, row1, rp, ci, v, z);
+  const int row = row0 + threadIdx.x;
+  if (row < row1) tout[row] = r[row] - s;
+}
+
+// plain y = A x (FP64), for the public amg_spmv
+template <int R>
+__global__ void __launch_bounds__(R) k_spmv(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                            const double* __restrict__ v, const double* __restrict__ x,
+                                            double* __restrict__ y) {
+  __shared__ __align__(16) TileSmem<double> sm;
+  const int row0 = blockIdx.x * R, row1 = min(row0 + R, n);
+  const double s = tile_row_dot<R, double, double, double>(sm, row0, row1, rp, ci, v, x);
+  const int row = row0 + threadIdx.x;
+  if (row < row1) y[row] = s;
 }
 
 // r_c[J] = sum over the members i of aggregate J (ascending) of t_i
@@ -101,47 +161,43 @@ __global__ void k_zero(int n, VT* __restrict__ a, const int* skip) {
   if (i < n) a[i] = (VT)0;
 }
 
-// plain y = A x (FP64), for the public amg_spmv
-template <int G>
-__global__ void __launch_bounds__(AMG_BLOCK) k_spmv(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                    const double* __restrict__ v, const double* __restrict__ x,
-                                                    double* __restrict__ y) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int row = (int)(t / G), lane = (int)(t % G);
-  if (row >= n) return;
-  double s = 0.0;
-  for (int p = rp[row] + lane; p < rp[row + 1]; p += G) s += v[p] * x[ci[p]];
-  s = group_sum<G>(s);
-  if (lane == 0) y[row] = s;
-}
-
 // ---------------------------------------------------------------------------
-// Alg. 1 kernels (FP64).  Persistent grids of red_grid blocks; the scalar work
-// of each step is done by the last block of the grid-wide reduction.
+// Alg. 1 kernels (FP64, level-0 matrix).  The row kernels run a persistent
+// grid of red_grid blocks over the row tiles; the scalar work of each step is
+// done by the last block of the grid-wide reduction (fixed order: the result
+// does not depend on timing).
 
-// r = b - A u;  |r|^2, |b|^2;  iteration 0 bookkeeping
-template <int G>
-__global__ void __launch_bounds__(AMG_BLOCK) k_fcg_init(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                        const double* __restrict__ v, const double* __restrict__ b,
-                                                        const double* __restrict__ u, double* __restrict__ r,
-                                                        FcgState* st, double* partial, unsigned* counter) {
-  __shared__ double sm[64];
+enum { RES_INIT = 0, RES_TRUE = 1, RES_NORM = 2 };
+
+// RES_INIT: r = b - A u, |r|^2, |b|^2, iteration-0 bookkeeping.
+// RES_TRUE: r = b - A u when the recursive residual dropped below tol
+//           (need_true = 1) or periodically in mixed precision (need_true = 2).
+// RES_NORM: |b - A u| / |b| only (exit report after breakdown / maxit).
+template <int R, int MODE>
+__global__ void __launch_bounds__(R) k_fcg_resid(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                 const double* __restrict__ v, const double* __restrict__ b,
+                                                 const double* __restrict__ u, double* __restrict__ r, FcgState* st,
+                                                 double* partial, unsigned* counter) {
+  if (MODE == RES_TRUE && (st->done || !st->need_true)) return;
+  __shared__ __align__(16) TileSmem<double> sm;
+  __shared__ double red[64];
   double acc[2] = {0.0, 0.0};
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * G; t += stride) {
-    int row = (int)(t / G), lane = (int)(t % G);
-    double s = 0.0;
-    for (int p = rp[row] + lane; p < rp[row + 1]; p += G) s += v[p] * u[ci[p]];
-    s = group_sum<G>(s);
-    if (lane == 0) {
-      double bi = b[row], ri = bi - s;
-      r[row] = ri;
+  const int ntiles = (n + R - 1) / R;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int row0 = tile * R, row1 = min(row0 + R, n);
+    const double s = tile_row_dot<R, double, double, double>(sm, row0, row1, rp, ci, v, u);
+    const int row = row0 + threadIdx.x;
+    if (row < row1) {
+      const double bi = b[row], ri = bi - s;
+      if (MODE != RES_NORM) r[row] = ri;
       acc[0] += ri * ri;
-      acc[1] += bi * bi;
+      if (MODE == RES_INIT) acc[1] += bi * bi;
     }
+    __syncthreads();
   }
-  if (grid_sum<2>(acc, partial, counter, sm) && threadIdx.x == 0) {
-    double nb = sqrt(acc[1]);
+  if (!grid_sum<2>(acc, partial, counter, red) || threadIdx.x != 0) return;
+  if (MODE == RES_INIT) {
+    const double nb = sqrt(acc[1]);
     st->nb = nb;
     st->it = 0;
     st->need_true = 0;
@@ -153,60 +209,80 @@ __global__ void __launch_bounds__(AMG_BLOCK) k_fcg_init(int n, const int32_t* __
       if (st->hist_len > 0) st->hist[0] = 0.0;
       st->done = 1;
     } else {
-      double res = sqrt(acc[0]) / nb;
+      const double res = sqrt(acc[0]) / nb;
       st->res = res;
       if (st->hist_len > 0) st->hist[0] = res;
       st->true_res = res;
       st->done = (res < st->tol) || (st->maxit <= 0);
       if (!(res < st->tol) && st->maxit <= 0) st->status = AMG_NOT_CONVERGED;
     }
+  } else if (MODE == RES_TRUE) {
+    const double tr = sqrt(acc[0]) / st->nb;
+    const int it = st->it;
+    st->true_res = tr;
+    if (tr < st->tol) {
+      if (st->need_true == 2 && it < st->hist_len) st->hist[it] = tr;
+      st->res = tr;
+      st->status = AMG_OK;
+      st->done = 1;
+    } else {
+      if (it < st->hist_len) st->hist[it] = tr;
+      st->res = tr;
+      if (it >= st->maxit) {
+        st->status = AMG_NOT_CONVERGED;
+        st->done = 1;
+      }
+    }
+    st->need_true = 0;
+  } else {
+    st->true_res = st->nb > 0 ? sqrt(acc[0]) / st->nb : 0.0;
   }
 }
 
 // v = A w;  alpha = w.r, beta = w.v, gamma = w.q;  rho and the step scalars
-template <int G>
-__global__ void __launch_bounds__(AMG_BLOCK) k_fcg_spmv_dots(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                             const double* __restrict__ v, const double* __restrict__ w,
-                                                             const double* __restrict__ r, const double* __restrict__ q,
-                                                             double* __restrict__ vout, FcgState* st, double* partial,
-                                                             unsigned* counter) {
+template <int R>
+__global__ void __launch_bounds__(R) k_fcg_spmv_dots(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                     const double* __restrict__ v, const double* __restrict__ w,
+                                                     const double* __restrict__ r, const double* __restrict__ q,
+                                                     double* __restrict__ vout, FcgState* st, double* partial,
+                                                     unsigned* counter) {
   if (st->done) return;
-  __shared__ double sm[96];
+  __shared__ __align__(16) TileSmem<double> sm;
+  __shared__ double red[96];
   const bool first = st->it == 0;
   double acc[3] = {0.0, 0.0, 0.0};
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * G; t += stride) {
-    int row = (int)(t / G), lane = (int)(t % G);
-    double s = 0.0;
-    for (int p = rp[row] + lane; p < rp[row + 1]; p += G) s += v[p] * w[ci[p]];
-    s = group_sum<G>(s);
-    if (lane == 0) {
-      double wi = w[row];
+  const int ntiles = (n + R - 1) / R;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int row0 = tile * R, row1 = min(row0 + R, n);
+    const double s = tile_row_dot<R, double, double, double>(sm, row0, row1, rp, ci, v, w);
+    const int row = row0 + threadIdx.x;
+    if (row < row1) {
+      const double wi = w[row];
       vout[row] = s;
       acc[0] += wi * r[row];
       acc[1] += wi * s;
       if (!first) acc[2] += wi * q[row];
     }
+    __syncthreads();
   }
-  if (grid_sum<3>(acc, partial, counter, sm) && threadIdx.x == 0) {
-    if (st->timing) return;
-    double alpha = acc[0], beta = acc[1], gamma = acc[2];
-    double rho_new, g;
-    if (first) {
-      rho_new = beta;
-      g = 0.0;
-    } else {
-      rho_new = beta - gamma * gamma / st->rho;
-      g = gamma / st->rho;
-    }
-    if (!(rho_new > 0.0) || !isfinite(rho_new)) {
-      st->status = AMG_ERR_BREAKDOWN;
-      st->done = 1;
-    } else {
-      st->g = g;
-      st->a = alpha / rho_new;
-      st->rho = rho_new;
-    }
+  if (!grid_sum<3>(acc, partial, counter, red) || threadIdx.x != 0) return;
+  if (st->timing) return;
+  const double alpha = acc[0], beta = acc[1], gamma = acc[2];
+  double rho_new, g;
+  if (first) {
+    rho_new = beta;
+    g = 0.0;
+  } else {
+    rho_new = beta - gamma * gamma / st->rho;
+    g = gamma / st->rho;
+  }
+  if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+    st->status = AMG_ERR_BREAKDOWN;
+    st->done = 1;
+  } else {
+    st->g = g;
+    st->a = alpha / rho_new;
+    st->rho = rho_new;
   }
 }
 
@@ -216,7 +292,7 @@ __global__ void __launch_bounds__(AMG_BLOCK) k_fcg_axpy(int n, const double* __r
                                                         double* __restrict__ u, double* __restrict__ r, FcgState* st,
                                                         double* partial, unsigned* counter) {
   if (st->done) return;
-  __shared__ double sm[32];
+  __shared__ double red[32];
   const bool first = st->it == 0;
   const double g = st->g, a = st->a;
   double acc[1] = {0.0};
@@ -233,114 +309,49 @@ __global__ void __launch_bounds__(AMG_BLOCK) k_fcg_axpy(int n, const double* __r
     d[i] = di;
     q[i] = qi;
     u[i] += a * di;
-    double ri = r[i] - a * qi;
+    const double ri = r[i] - a * qi;
     r[i] = ri;
     acc[0] += ri * ri;
   }
-  if (grid_sum<1>(acc, partial, counter, sm) && threadIdx.x == 0) {
-    if (st->timing) return;
-    int it = st->it + 1;
-    st->it = it;
-    double res = sqrt(acc[0]) / st->nb;
-    st->res = res;
-    if (it < st->hist_len) st->hist[it] = res;
-    bool periodic = st->mixed && st->true_every > 0 && (it % st->true_every) == 0;
-    st->need_true = (res < st->tol) ? 1 : (periodic ? 2 : 0);
-    if (!st->need_true && it >= st->maxit) {
-      st->status = AMG_NOT_CONVERGED;
-      st->done = 1;
-    }
+  if (!grid_sum<1>(acc, partial, counter, red) || threadIdx.x != 0) return;
+  if (st->timing) return;
+  const int it = st->it + 1;
+  st->it = it;
+  const double res = sqrt(acc[0]) / st->nb;
+  st->res = res;
+  if (it < st->hist_len) st->hist[it] = res;
+  const bool periodic = st->mixed && st->true_every > 0 && (it % st->true_every) == 0;
+  st->need_true = (res < st->tol) ? 1 : (periodic ? 2 : 0);
+  if (!st->need_true && it >= st->maxit) {
+    st->status = AMG_NOT_CONVERGED;
+    st->done = 1;
   }
-}
-
-// true residual r = b - A u when the recursive residual dropped below tol
-// (need_true = 1) or periodically in mixed precision (need_true = 2)
-template <int G>
-__global__ void __launch_bounds__(AMG_BLOCK) k_fcg_true(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                        const double* __restrict__ v, const double* __restrict__ b,
-                                                        const double* __restrict__ u, double* __restrict__ r,
-                                                        FcgState* st, double* partial, unsigned* counter) {
-  if (st->done || !st->need_true) return;
-  __shared__ double sm[32];
-  double acc[1] = {0.0};
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * G; t += stride) {
-    int row = (int)(t / G), lane = (int)(t % G);
-    double s = 0.0;
-    for (int p = rp[row] + lane; p < rp[row + 1]; p += G) s += v[p] * u[ci[p]];
-    s = group_sum<G>(s);
-    if (lane == 0) {
-      double ri = b[row] - s;
-      r[row] = ri;
-      acc[0] += ri * ri;
-    }
-  }
-  if (grid_sum<1>(acc, partial, counter, sm) && threadIdx.x == 0) {
-    double tr = sqrt(acc[0]) / st->nb;
-    int it = st->it;
-    st->true_res = tr;
-    if (tr < st->tol) {
-      if (st->need_true == 2 && it < st->hist_len) st->hist[it] = tr;
-      st->res = tr;
-      st->status = AMG_OK;
-      st->done = 1;
-    } else {
-      if (it < st->hist_len) st->hist[it] = tr;
-      st->res = tr;
-      if (it >= st->maxit) {
-        st->status = AMG_NOT_CONVERGED;
-        st->done = 1;
-      }
-    }
-    st->need_true = 0;
-  }
-}
-
-// |b - A u| / |b| without touching r (exit report after breakdown / maxit)
-template <int G>
-__global__ void __launch_bounds__(AMG_BLOCK) k_true_norm(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                         const double* __restrict__ v, const double* __restrict__ b,
-                                                         const double* __restrict__ u, FcgState* st, double* partial,
-                                                         unsigned* counter) {
-  __shared__ double sm[32];
-  double acc[1] = {0.0};
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * G; t += stride) {
-    int row = (int)(t / G), lane = (int)(t % G);
-    double s = 0.0;
-    for (int p = rp[row] + lane; p < rp[row + 1]; p += G) s += v[p] * u[ci[p]];
-    s = group_sum<G>(s);
-    if (lane == 0) {
-      double ri = b[row] - s;
-      acc[0] += ri * ri;
-    }
-  }
-  if (grid_sum<1>(acc, partial, counter, sm) && threadIdx.x == 0) st->true_res = st->nb > 0 ? sqrt(acc[0]) / st->nb : 0.0;
 }
 
 // ---------------------------------------------------------------------------
-// launch helpers (dispatch on the lanes per row)
+// launch helpers (dispatch on the tile height)
 
-#define DISPATCH_G(G, CALL)            \
-  switch (G) {                         \
-    case 2: { constexpr int GG = 2; CALL; } break;   \
-    case 4: { constexpr int GG = 4; CALL; } break;   \
-    case 8: { constexpr int GG = 8; CALL; } break;   \
-    case 16: { constexpr int GG = 16; CALL; } break; \
-    default: { constexpr int GG = 32; CALL; } break; \
+#define DISPATCH_R(RR, CALL)                          \
+  switch (RR) {                                       \
+    case 256: { constexpr int TR = 256; CALL; } break; \
+    case 128: { constexpr int TR = 128; CALL; } break; \
+    case 64: { constexpr int TR = 64; CALL; } break;   \
+    default: { constexpr int TR = 32; CALL; } break;   \
   }
 
 template <typename MT, typename VT, typename OT>
 static void launch_sweep(cudaStream_t s, const Level& L, const MT* vals, const VT* dinv, const VT* r, const VT* z, OT* out,
                          const int* skip) {
-  int nb = amg_blocks((int64_t)L.n * L.G);
-  DISPATCH_G(L.G, (k_sweep<GG, MT, VT, OT><<<nb, AMG_BLOCK, 0, s>>>(L.n, L.rp, L.ci, vals, dinv, r, z, out, skip)));
+  const int R = L.R;
+  const int nb = (L.n + R - 1) / R;
+  DISPATCH_R(R, (k_sweep<TR, MT, VT, OT><<<nb, TR, 0, s>>>(L.n, L.rp, L.ci, vals, dinv, r, z, out, skip)));
 }
 
 template <typename MT, typename VT>
 static void launch_resid(cudaStream_t s, const Level& L, const MT* vals, const VT* r, const VT* z, VT* t, const int* skip) {
-  int nb = amg_blocks((int64_t)L.n * L.G);
-  DISPATCH_G(L.G, (k_resid<GG, MT, VT><<<nb, AMG_BLOCK, 0, s>>>(L.n, L.rp, L.ci, vals, r, z, t, skip)));
+  const int R = L.R;
+  const int nb = (L.n + R - 1) / R;
+  DISPATCH_R(R, (k_resid<TR, MT, VT><<<nb, TR, 0, s>>>(L.n, L.rp, L.ci, vals, r, z, t, skip)));
 }
 
 // ---------------------------------------------------------------------------
@@ -523,14 +534,14 @@ static void record_iteration(VRec& R, bool precond) {
     k_copy<double, double><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, h->r, h->w, skip);
     R.add(16.0 * L.n);
   }
-  DISPATCH_G(L.G, (k_fcg_spmv_dots<GG><<<g, AMG_BLOCK, 0, R.s>>>(L.n, L.rp, L.ci, L.v, h->w, h->r, h->q, h->v, st,
-                                                                 h->partial, h->counter)));
+  DISPATCH_R(L.Rd, (k_fcg_spmv_dots<TR><<<g, TR, 0, R.s>>>(L.n, L.rp, L.ci, L.v, h->w, h->r, h->q, h->v, st,
+                                                          h->partial, h->counter)));
   R.add(bytes_spmv_dots(L));
-  k_fcg_axpy<<<g, AMG_BLOCK, 0, R.s>>>(L.n, h->w, h->v, h->d, h->q, h->u, h->r, st, h->partial, h->counter);
+  k_fcg_axpy<<<h->ax_grid, AMG_BLOCK, 0, R.s>>>(L.n, h->w, h->v, h->d, h->q, h->u, h->r, st, h->partial, h->counter);
   R.add(bytes_axpy(L));
   // the true-residual check moves data only once per solve (at convergence)
-  DISPATCH_G(L.G, (k_fcg_true<GG><<<g, AMG_BLOCK, 0, R.s>>>(L.n, L.rp, L.ci, L.v, h->b, h->u, h->r, st,
-                                                            h->partial, h->counter)));
+  DISPATCH_R(L.Rd, (k_fcg_resid<TR, RES_TRUE><<<g, TR, 0, R.s>>>(L.n, L.rp, L.ci, L.v, h->b, h->u, h->r, st,
+                                                                 h->partial, h->counter)));
   R.add(0.0);
 }
 
@@ -579,9 +590,10 @@ amg_status amg_prepare_solve(amg_handle* h) {
   int dev = 0, sms = 148;
   AMG_CK(h, cudaGetDevice(&dev));
   AMG_CK(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  int64_t want = amg_blocks((int64_t)n * h->L[0].G);
-  h->red_grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 4));
-  AMG_ALLOC(h, h->partial, double, (size_t)h->red_grid * 4);
+  const int64_t tiles = (n + h->L[0].Rd - 1) / h->L[0].Rd;
+  h->red_grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 8));
+  h->ax_grid = (int)std::max<int64_t>(1, std::min<int64_t>(amg_blocks(n), (int64_t)sms * 8));
+  AMG_ALLOC(h, h->partial, double, (size_t)std::max(h->red_grid, h->ax_grid) * 4);
   AMG_ALLOC(h, h->counter, unsigned, 4);
   AMG_ALLOC(h, h->st, FcgState, 1);
   AMG_CK(h, cudaMallocHost((void**)&h->st_host, sizeof(FcgState)));
@@ -667,8 +679,8 @@ static amg_status run_fcg(amg_handle* h, bool precond, double tol, int maxit, in
   hs->hist_len = maxit + 1;
   AMG_CK(h, cudaMemcpyAsync(h->st, hs, sizeof(FcgState), cudaMemcpyHostToDevice, s));
   const int g = h->red_grid;
-  DISPATCH_G(L.G, (k_fcg_init<GG><<<g, AMG_BLOCK, 0, s>>>(n, L.rp, L.ci, L.v, h->b, h->u, h->r, h->st,
-                                                          h->partial, h->counter)));
+  DISPATCH_R(L.Rd, (k_fcg_resid<TR, RES_INIT><<<g, TR, 0, s>>>(n, L.rp, L.ci, L.v, h->b, h->u, h->r, h->st,
+                                                               h->partial, h->counter)));
   AMG_CK(h, cudaGetLastError());
   AMG_CK(h, cudaMemcpyAsync(hs, h->st, sizeof(FcgState), cudaMemcpyDeviceToHost, s));
   AMG_CK(h, cudaStreamSynchronize(s));
@@ -688,8 +700,8 @@ static amg_status run_fcg(amg_handle* h, bool precond, double tol, int maxit, in
     AMG_CK(h, cudaStreamSynchronize(s));
   }
   if (hs->status != AMG_OK && hs->nb > 0.0) {
-    DISPATCH_G(L.G, (k_true_norm<GG><<<g, AMG_BLOCK, 0, s>>>(n, L.rp, L.ci, L.v, h->b, h->u, h->st, h->partial,
-                                                             h->counter)));
+    DISPATCH_R(L.Rd, (k_fcg_resid<TR, RES_NORM><<<g, TR, 0, s>>>(n, L.rp, L.ci, L.v, h->b, h->u, nullptr, h->st,
+                                                                 h->partial, h->counter)));
     AMG_CK(h, cudaMemcpyAsync(hs, h->st, sizeof(FcgState), cudaMemcpyDeviceToHost, s));
     AMG_CK(h, cudaStreamSynchronize(s));
   }
@@ -760,8 +772,8 @@ extern "C" amg_status amg_spmv(amg_handle* h, int32_t level, const double* x, do
   if (!h) return AMG_ERR_INVALID_ARG;
   if (level < 0 || level >= h->nl || !x || !y) return amg_fail(h, AMG_ERR_INVALID_ARG, "bad level or pointer");
   Level& L = h->L[level];
-  int nb = amg_blocks((int64_t)L.n * L.G);
-  DISPATCH_G(L.G, (k_spmv<GG><<<nb, AMG_BLOCK, 0, h->stream>>>(L.n, L.rp, L.ci, L.v, x, y)));
+  const int nb = (L.n + L.Rd - 1) / L.Rd;
+  DISPATCH_R(L.Rd, (k_spmv<TR><<<nb, TR, 0, h->stream>>>(L.n, L.rp, L.ci, L.v, x, y)));
   AMG_CK(h, cudaGetLastError());
   AMG_CK(h, cudaStreamSynchronize(h->stream));
   return AMG_OK;
@@ -835,12 +847,12 @@ static amg_status launch_one(amg_handle* h, int which, int k) {
     }
     case 4:
       if (k != 0) return amg_fail(h, AMG_ERR_INVALID_ARG, "outer kernels run on level 0");
-      DISPATCH_G(L.G, (k_fcg_spmv_dots<GG><<<g, AMG_BLOCK, 0, s>>>(L.n, L.rp, L.ci, L.v, h->w, h->r, h->q, h->v, h->st,
-                                                                   h->partial, h->counter)));
+      DISPATCH_R(L.Rd, (k_fcg_spmv_dots<TR><<<g, TR, 0, s>>>(L.n, L.rp, L.ci, L.v, h->w, h->r, h->q, h->v, h->st,
+                                                            h->partial, h->counter)));
       break;
     case 5:
       if (k != 0) return amg_fail(h, AMG_ERR_INVALID_ARG, "outer kernels run on level 0");
-      k_fcg_axpy<<<g, AMG_BLOCK, 0, s>>>(L.n, h->w, h->v, h->d, h->q, h->u, h->r, h->st, h->partial, h->counter);
+      k_fcg_axpy<<<h->ax_grid, AMG_BLOCK, 0, s>>>(L.n, h->w, h->v, h->d, h->q, h->u, h->r, h->st, h->partial, h->counter);
       break;
     default:
       return amg_fail(h, AMG_ERR_INVALID_ARG, "unknown kernel id %d", which);
