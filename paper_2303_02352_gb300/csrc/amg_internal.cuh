@@ -56,6 +56,8 @@ struct Level {
   int maxrow = 0;            // longest row (nonzeros)
   int R = 256;               // tile height of the row kernels with this level's V-cycle value type
   int Rd = 256;              // tile height with FP64 values (outer kernels, amg_spmv)
+  bool pipe = false;         // every tile fits a pipeline stage (V-cycle value type)
+  bool piped = false;        // same with FP64 values
   int32_t* rp = nullptr;     // CSR (FP64 values)
   int32_t* ci = nullptr;
   double* v = nullptr;
@@ -98,6 +100,8 @@ struct amg_handle {
   int* zero_flag = nullptr;    // a device int that stays 0 (skip flag of standalone V-cycles)
   int red_grid = 0;            // persistent grid of the outer row kernels
   int ax_grid = 0;             // grid of the fused axpys
+  int stages = 2;              // pipeline depth of the row kernels (2 measured best: more stages cost resident blocks)
+  int use_pipe = 1;            // 0: non-pipelined tiled row kernels
   cudaGraphExec_t g_vcycle = nullptr;
   cudaGraphExec_t g_iter = nullptr;
   cudaGraphExec_t g_iter_cg = nullptr;
@@ -144,6 +148,8 @@ static inline int amg_tile_rows(int maxrow, int value_bytes) {
 
 void amg_set_setup_error(const std::string& msg);  // message for amg_last_error(NULL)
 amg_status amg_level_diag(amg_handle* h, int k);   // l1 norms and D = omega / l1 of level k
+
+int amg_num_sms();  // multiprocessors of the current device
 
 // solve-phase internals (solve.cu)
 amg_status amg_prepare_solve(amg_handle* h);

@@ -1,0 +1,257 @@
+// Persistent TMA-pipelined row kernels (included by solve.cu).
+//
+// A block owns tiles of R consecutive rows, round-robin over the grid.  The
+// nonzeros of a tile are contiguous in CSR; one thread issues two 1D bulk
+// tensor copies (cp.async.bulk, the TMA engine) that move the tile's values and
+// column indices into a shared-memory stage and signal an mbarrier.  S stages
+// rotate: while the block computes tile k, the copies of tiles k+1 .. k+S-1 are
+// in flight, so HBM sees a continuous stream.  Each thread finishes one row
+// (one multiply-add per nonzero, no shuffle reduction: FP64 issue rate is a
+// co-limit on this part) and gathers the vector through L1/L2.
+//
+// Every mbarrier wait is bounded; on expiry the kernel sets ST_TIMEOUT in the
+// device flags, drains its copies with a bounded wait and ends its tile loop.
+#pragma once
+
+#include "amg_internal.cuh"
+
+#define PIPE_TILE_BYTES 24576
+#define PIPE_WAIT_LIMIT (1u << 22)
+
+template <typename MT>
+struct PipeTile {
+  static constexpr int VE = 16 / (int)sizeof(MT);
+  static constexpr int CAP = PIPE_TILE_BYTES / ((int)sizeof(MT) + 4);
+  MT v[CAP + 2 * VE];
+  int32_t c[CAP + 8];
+};
+
+template <typename MT, int S>
+struct PipeSmem {
+  PipeTile<MT> st[S];
+  unsigned long long bar[S];
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: true when the phase completed
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < PIPE_WAIT_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+enum { PM_SWEEP = 0, PM_RESID = 1, PM_SPMV = 2, PM_DOTS = 3, PM_RINIT = 4, PM_RTRUE = 5, PM_RNORM = 6 };
+
+template <typename MT, typename VT, typename OT>
+struct RowArgs {
+  int n;
+  const int32_t* rp;
+  const int32_t* ci;
+  const MT* v;
+  const VT* x;      // gathered vector (z, w or u)
+  const VT* dinv;   // sweep
+  const VT* r;      // sweep / residual: level right-hand side; dots: FCG r
+  const VT* b;      // FCG right-hand side
+  const VT* q;      // dots
+  OT* out;          // sweep: z_out, resid: t, spmv: y, dots: v, rinit/rtrue: r
+  const int* skip;  // V-cycle modes
+  FcgState* st;     // FCG modes
+  double* partial;
+  unsigned* counter;
+  int* flags;
+};
+
+template <int R, int S, int MODE, typename MT, typename VT, typename OT>
+__global__ void __launch_bounds__(R) k_rows_pipe(const RowArgs<MT, VT, OT> a) {
+  if constexpr (MODE == PM_SWEEP || MODE == PM_RESID) {
+    if (*a.skip) return;
+  } else if constexpr (MODE == PM_DOTS) {
+    if (a.st->done) return;
+  } else if constexpr (MODE == PM_RTRUE) {
+    if (a.st->done || !a.st->need_true) return;
+  }
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  auto* P = reinterpret_cast<PipeSmem<MT, S>*>(smem_raw);
+  __shared__ double red[96];
+  constexpr int VE = PipeTile<MT>::VE;
+  const int n = a.n;
+  const int ntiles = (n + R - 1) / R;
+  const int G = gridDim.x;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&P->bar[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](int k, int stage) {  // thread 0: copies of this block's k-th tile
+    const int tile = blockIdx.x + k * G;
+    if (tile >= ntiles) return;
+    const int row0 = tile * R, row1 = min(row0 + R, n);
+    const int p0 = __ldg(&a.rp[row0]), p1 = __ldg(&a.rp[row1]);
+    const int av = p0 & ~(VE - 1), ac = p0 & ~3;
+    const uint32_t bv = (uint32_t)(((p1 - av) * (int)sizeof(MT) + 15) & ~15);
+    const uint32_t bc = (uint32_t)(((p1 - ac) * 4 + 15) & ~15);
+    mbar_expect_tx(&P->bar[stage], bv + bc);
+    tma_load_1d(P->st[stage].v, a.v + av, bv, &P->bar[stage]);
+    tma_load_1d(P->st[stage].c, a.ci + ac, bc, &P->bar[stage]);
+  };
+  if (threadIdx.x == 0)
+    for (int k = 0; k < S; ++k) issue(k, k);
+
+  double acc[3] = {0.0, 0.0, 0.0};
+  const bool first = (MODE == PM_DOTS) ? (a.st->it == 0) : false;
+  int k = 0;
+  for (;; ++k) {
+    const int tile = blockIdx.x + k * G;
+    if (tile >= ntiles) break;
+    const int stage = k % S;
+    const uint32_t parity = (uint32_t)((k / S) & 1);
+    const int row0 = tile * R, row1 = min(row0 + R, n);
+    const int row = row0 + (int)threadIdx.x;
+    const bool live = row < row1;
+    const int p0 = __ldg(&a.rp[row0]);
+    int q0 = 0, q1 = 0;
+    VT own = 0, rr = 0, dd = 0, qq = 0;
+    if (live) {
+      q0 = __ldg(&a.rp[row]);
+      q1 = __ldg(&a.rp[row + 1]);
+      if constexpr (MODE == PM_SWEEP) {
+        own = __ldg(&a.x[row]);
+        rr = __ldg(&a.r[row]);
+        dd = __ldg(&a.dinv[row]);
+      } else if constexpr (MODE == PM_RESID) {
+        rr = __ldg(&a.r[row]);
+      } else if constexpr (MODE == PM_DOTS) {
+        own = __ldg(&a.x[row]);
+        rr = __ldg(&a.r[row]);
+        if (!first) qq = __ldg(&a.q[row]);
+      } else if constexpr (MODE == PM_RINIT || MODE == PM_RTRUE || MODE == PM_RNORM) {
+        rr = __ldg(&a.b[row]);
+      }
+    }
+    const bool ok = mbar_wait(&P->bar[stage], parity);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(a.flags, ST_TIMEOUT);
+        for (int j = 0; j < S; ++j) {  // drain the copies this block may still have in flight
+          const int kk = k + j;
+          if (blockIdx.x + kk * G < ntiles) mbar_wait(&P->bar[kk % S], (uint32_t)((kk / S) & 1));
+        }
+      }
+      __syncthreads();
+      break;
+    }
+    const int av = p0 & ~(VE - 1), ac = p0 & ~3;
+    const PipeTile<MT>& T = P->st[stage];
+    VT s = 0;
+#pragma unroll 8
+    for (int q = q0; q < q1; ++q) s += (VT)to_acc(T.v[q - av]) * __ldg(&a.x[T.c[q - ac]]);
+    if (live) {
+      if constexpr (MODE == PM_SWEEP) {
+        a.out[row] = (OT)(own + dd * (rr - s));
+      } else if constexpr (MODE == PM_RESID) {
+        a.out[row] = (OT)(rr - s);
+      } else if constexpr (MODE == PM_SPMV) {
+        a.out[row] = (OT)s;
+      } else if constexpr (MODE == PM_DOTS) {
+        a.out[row] = (OT)s;
+        acc[0] += (double)own * (double)rr;
+        acc[1] += (double)own * (double)s;
+        if (!first) acc[2] += (double)own * (double)qq;
+      } else {
+        const double ri = (double)rr - (double)s;
+        if constexpr (MODE != PM_RNORM) a.out[row] = (OT)ri;
+        acc[0] += ri * ri;
+        if constexpr (MODE == PM_RINIT) acc[1] += (double)rr * (double)rr;
+      }
+    }
+    __syncthreads();  // every thread is done with this stage
+    if (threadIdx.x == 0) issue(k + S, stage);
+  }
+
+  if constexpr (MODE == PM_DOTS) {
+    if (!grid_sum<3>(acc, a.partial, a.counter, red) || threadIdx.x != 0) return;
+    FcgState* st = a.st;
+    if (st->timing) return;
+    const double alpha = acc[0], beta = acc[1], gamma = acc[2];
+    double rho_new, g;
+    if (first) {
+      rho_new = beta;
+      g = 0.0;
+    } else {
+      rho_new = beta - gamma * gamma / st->rho;
+      g = gamma / st->rho;
+    }
+    if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+      st->status = AMG_ERR_BREAKDOWN;
+      st->done = 1;
+    } else {
+      st->g = g;
+      st->a = alpha / rho_new;
+      st->rho = rho_new;
+    }
+  } else if constexpr (MODE == PM_RINIT || MODE == PM_RTRUE || MODE == PM_RNORM) {
+    double acc2[2] = {acc[0], acc[1]};
+    if (!grid_sum<2>(acc2, a.partial, a.counter, red) || threadIdx.x != 0) return;
+    fcg_residual_epilogue<MODE == PM_RINIT ? RES_INIT : (MODE == PM_RTRUE ? RES_TRUE : RES_NORM)>(a.st, acc2);
+  }
+}
+
+// grid of a persistent pipelined kernel: one wave of resident blocks, at most
+// one block per tile
+template <int R, int S, int MODE, typename MT, typename VT, typename OT>
+static int pipe_grid(int n) {
+  static int bps = -1;
+  constexpr int smem = (int)sizeof(PipeSmem<MT, S>);
+  auto kern = k_rows_pipe<R, S, MODE, MT, VT, OT>;
+  if (bps < 0) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, R, smem);
+    bps = b < 1 ? 1 : b;
+  }
+  const int ntiles = (n + R - 1) / R;
+  const int g = amg_num_sms() * bps;
+  return ntiles < g ? ntiles : g;
+}
+
+template <int R, int S, int MODE, typename MT, typename VT, typename OT>
+static void launch_pipe(cudaStream_t s, const RowArgs<MT, VT, OT>& a) {
+  const int grid = pipe_grid<R, S, MODE, MT, VT, OT>(a.n);
+  constexpr int smem = (int)sizeof(PipeSmem<MT, S>);
+  k_rows_pipe<R, S, MODE, MT, VT, OT><<<grid, R, smem, s>>>(a);
+}

@@ -15,6 +15,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <chrono>
+#include <cstdlib>
 
 #include "amg_internal.cuh"
 
@@ -741,8 +742,11 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
     if (st0 != AMG_OK) return st0;
     AMG_CK(h, cudaMemsetAsync(h->dev_flags, 0, sizeof(int), s));
     L.maxrow = mr;
+    const int vb = L.lowp ? ((h->p.precision == AMG_FP32_BF16FINE && k == 0) ? 2 : 4) : 8;
     L.Rd = amg_tile_rows(mr, 8);
-    L.R = amg_tile_rows(mr, L.lowp ? ((h->p.precision == AMG_FP32_BF16FINE && k == 0) ? 2 : 4) : 8);
+    L.R = amg_tile_rows(mr, vb);
+    L.piped = h->use_pipe && (int64_t)L.Rd * mr <= 24576 / 12;
+    L.pipe = h->use_pipe && (int64_t)L.R * mr <= 24576 / (vb + 4);
     AMG_ALLOC(h, L.l1, double, L.n);
     AMG_ALLOC(h, L.dinv, double, L.n);
     if (L.lowp) {
@@ -775,6 +779,8 @@ extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* str
   if (p) h->p = *p;
   else amg_params_default(&h->p);
   h->stream = (cudaStream_t)stream;
+  if (const char* e = getenv("AMG_PIPE")) h->use_pipe = atoi(e);
+  if (const char* e = getenv("AMG_STAGES")) h->stages = atoi(e);
   amg_status st = setup_impl(h, A);
   if (st != AMG_OK) {
     amg_set_setup_error(h->err);

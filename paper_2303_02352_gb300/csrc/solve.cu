@@ -169,33 +169,12 @@ __global__ void k_zero(int n, VT* __restrict__ a, const int* skip) {
 
 enum { RES_INIT = 0, RES_TRUE = 1, RES_NORM = 2 };
 
-// RES_INIT: r = b - A u, |r|^2, |b|^2, iteration-0 bookkeeping.
-// RES_TRUE: r = b - A u when the recursive residual dropped below tol
-//           (need_true = 1) or periodically in mixed precision (need_true = 2).
-// RES_NORM: |b - A u| / |b| only (exit report after breakdown / maxit).
-template <int R, int MODE>
-__global__ void __launch_bounds__(R) k_fcg_resid(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                 const double* __restrict__ v, const double* __restrict__ b,
-                                                 const double* __restrict__ u, double* __restrict__ r, FcgState* st,
-                                                 double* partial, unsigned* counter) {
-  if (MODE == RES_TRUE && (st->done || !st->need_true)) return;
-  __shared__ __align__(16) TileSmem<double> sm;
-  __shared__ double red[64];
-  double acc[2] = {0.0, 0.0};
-  const int ntiles = (n + R - 1) / R;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int row0 = tile * R, row1 = min(row0 + R, n);
-    const double s = tile_row_dot<R, double, double, double>(sm, row0, row1, rp, ci, v, u);
-    const int row = row0 + threadIdx.x;
-    if (row < row1) {
-      const double bi = b[row], ri = bi - s;
-      if (MODE != RES_NORM) r[row] = ri;
-      acc[0] += ri * ri;
-      if (MODE == RES_INIT) acc[1] += bi * bi;
-    }
-    __syncthreads();
-  }
-  if (!grid_sum<2>(acc, partial, counter, red) || threadIdx.x != 0) return;
+// scalar bookkeeping after r = b - A u (acc[0] = |r|^2, acc[1] = |b|^2)
+// RES_INIT: iteration 0.  RES_TRUE: the stop test on the true residual, run
+// when the recursive residual dropped below tol (need_true = 1) or
+// periodically in mixed precision (need_true = 2).  RES_NORM: exit report.
+template <int MODE>
+__device__ __forceinline__ void fcg_residual_epilogue(FcgState* st, const double (&acc)[2]) {
   if (MODE == RES_INIT) {
     const double nb = sqrt(acc[1]);
     st->nb = nb;
@@ -237,6 +216,35 @@ __global__ void __launch_bounds__(R) k_fcg_resid(int n, const int32_t* __restric
   } else {
     st->true_res = st->nb > 0 ? sqrt(acc[0]) / st->nb : 0.0;
   }
+}
+
+// Non-pipelined variants (levels whose rows are too long for a pipeline tile).
+// RES_INIT: r = b - A u, |r|^2, |b|^2.  RES_TRUE: r = b - A u when asked.
+// RES_NORM: |b - A u| / |b| only.
+template <int R, int MODE>
+__global__ void __launch_bounds__(R) k_fcg_resid(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                 const double* __restrict__ v, const double* __restrict__ b,
+                                                 const double* __restrict__ u, double* __restrict__ r, FcgState* st,
+                                                 double* partial, unsigned* counter) {
+  if (MODE == RES_TRUE && (st->done || !st->need_true)) return;
+  __shared__ __align__(16) TileSmem<double> sm;
+  __shared__ double red[64];
+  double acc[2] = {0.0, 0.0};
+  const int ntiles = (n + R - 1) / R;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int row0 = tile * R, row1 = min(row0 + R, n);
+    const double s = tile_row_dot<R, double, double, double>(sm, row0, row1, rp, ci, v, u);
+    const int row = row0 + threadIdx.x;
+    if (row < row1) {
+      const double bi = b[row], ri = bi - s;
+      if (MODE != RES_NORM) r[row] = ri;
+      acc[0] += ri * ri;
+      if (MODE == RES_INIT) acc[1] += bi * bi;
+    }
+    __syncthreads();
+  }
+  if (!grid_sum<2>(acc, partial, counter, red) || threadIdx.x != 0) return;
+  fcg_residual_epilogue<MODE>(st, acc);
 }
 
 // v = A w;  alpha = w.r, beta = w.v, gamma = w.q;  rho and the step scalars
@@ -328,8 +336,21 @@ __global__ void __launch_bounds__(AMG_BLOCK) k_fcg_axpy(int n, const double* __r
   }
 }
 
+int amg_num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+#include "rows.cuh"
+
 // ---------------------------------------------------------------------------
-// launch helpers (dispatch on the tile height)
+// launch helpers (dispatch on the tile height and on the pipeline depth)
 
 #define DISPATCH_R(RR, CALL)                          \
   switch (RR) {                                       \
@@ -339,19 +360,69 @@ __global__ void __launch_bounds__(AMG_BLOCK) k_fcg_axpy(int n, const double* __r
     default: { constexpr int TR = 32; CALL; } break;   \
   }
 
+#define DISPATCH_S(SS, CALL)                          \
+  if ((SS) == 2) { constexpr int TS = 2; CALL; }      \
+  else if ((SS) == 4) { constexpr int TS = 4; CALL; } \
+  else { constexpr int TS = 3; CALL; }
+
+template <int MODE, typename MT, typename VT, typename OT>
+static void launch_rows(cudaStream_t s, int R, int S, const RowArgs<MT, VT, OT>& a) {
+  DISPATCH_R(R, DISPATCH_S(S, (launch_pipe<TR, TS, MODE, MT, VT, OT>(s, a))));
+}
+
 template <typename MT, typename VT, typename OT>
 static void launch_sweep(cudaStream_t s, const Level& L, const MT* vals, const VT* dinv, const VT* r, const VT* z, OT* out,
-                         const int* skip) {
+                         const int* skip, int* flags, int stages) {
   const int R = L.R;
+  if (L.pipe) {
+    RowArgs<MT, VT, OT> a{L.n, L.rp, L.ci, vals, z, dinv, r, nullptr, nullptr, out, skip, nullptr, nullptr, nullptr, flags};
+    launch_rows<PM_SWEEP>(s, R, stages, a);
+    return;
+  }
   const int nb = (L.n + R - 1) / R;
   DISPATCH_R(R, (k_sweep<TR, MT, VT, OT><<<nb, TR, 0, s>>>(L.n, L.rp, L.ci, vals, dinv, r, z, out, skip)));
 }
 
 template <typename MT, typename VT>
-static void launch_resid(cudaStream_t s, const Level& L, const MT* vals, const VT* r, const VT* z, VT* t, const int* skip) {
+static void launch_resid(cudaStream_t s, const Level& L, const MT* vals, const VT* r, const VT* z, VT* t, const int* skip,
+                         int* flags, int stages) {
   const int R = L.R;
+  if (L.pipe) {
+    RowArgs<MT, VT, VT> a{L.n, L.rp, L.ci, vals, z, nullptr, r, nullptr, nullptr, t, skip, nullptr, nullptr, nullptr, flags};
+    launch_rows<PM_RESID>(s, R, stages, a);
+    return;
+  }
   const int nb = (L.n + R - 1) / R;
   DISPATCH_R(R, (k_resid<TR, MT, VT><<<nb, TR, 0, s>>>(L.n, L.rp, L.ci, vals, r, z, t, skip)));
+}
+
+// outer kernels on level 0 (FP64 values)
+static void launch_dots(amg_handle* h, cudaStream_t s) {
+  Level& L = h->L[0];
+  if (L.piped) {
+    RowArgs<double, double, double> a{L.n, L.rp, L.ci, L.v, h->w, nullptr, h->r, nullptr, h->q, h->v,
+                                      nullptr, h->st, h->partial, h->counter, h->dev_flags};
+    launch_rows<PM_DOTS>(s, L.Rd, h->stages, a);
+    return;
+  }
+  DISPATCH_R(L.Rd, (k_fcg_spmv_dots<TR><<<h->red_grid, TR, 0, s>>>(L.n, L.rp, L.ci, L.v, h->w, h->r, h->q, h->v, h->st,
+                                                                   h->partial, h->counter)));
+}
+
+template <int MODE>
+static void launch_fcg_resid(amg_handle* h, cudaStream_t s) {
+  Level& L = h->L[0];
+  constexpr int PM = MODE == RES_INIT ? PM_RINIT : (MODE == RES_TRUE ? PM_RTRUE : PM_RNORM);
+  if (L.piped) {
+    RowArgs<double, double, double> a{L.n, L.rp, L.ci, L.v, h->u, nullptr, nullptr, h->b, nullptr,
+                                      MODE == RES_NORM ? nullptr : h->r, nullptr, h->st, h->partial, h->counter,
+                                      h->dev_flags};
+    launch_rows<PM>(s, L.Rd, h->stages, a);
+    return;
+  }
+  DISPATCH_R(L.Rd, (k_fcg_resid<TR, MODE><<<h->red_grid, TR, 0, s>>>(L.n, L.rp, L.ci, L.v, h->b, h->u,
+                                                                     MODE == RES_NORM ? nullptr : h->r, h->st,
+                                                                     h->partial, h->counter)));
 }
 
 // ---------------------------------------------------------------------------
@@ -397,7 +468,7 @@ static double* rec_coarse(VRec& R, int k, const double* r, double* final_out) {
   cur = o;
   for (int sw = 1; sw < sweeps; ++sw) {
     double* nxt = (sw == sweeps - 1 && final_out) ? final_out : (cur == za ? zb : za);
-    launch_sweep<double, double, double>(R.s, L, L.v, L.dinv, r, cur, nxt, R.skip);
+    launch_sweep<double, double, double>(R.s, L, L.v, L.dinv, r, cur, nxt, R.skip, R.h->dev_flags, R.h->stages);
     R.add(row_pass(L, 8.0) + 32.0 * n);
     cur = nxt;
   }
@@ -467,7 +538,7 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out) {
     R.add(sr * n + 2.0 * sx * n + rc_bytes);
     for (int sw = 1; sw < h->p.pre_sweeps; ++sw) {
       VT* nxt = cur == za ? zb : za;
-      launch_sweep<MT, VT, VT>(R.s, L, vals, dinv, r, cur, nxt, R.skip);
+      launch_sweep<MT, VT, VT>(R.s, L, vals, dinv, r, cur, nxt, R.skip, h->dev_flags, h->stages);
       R.add(row_pass(L, sv) + 4.0 * sx * n);
       cur = nxt;
     }
@@ -480,7 +551,7 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out) {
     R.add(sx * n);
   }
   // residual, restriction, coarse correction, prolongation
-  launch_resid<MT, VT>(R.s, L, vals, r, cur, t, R.skip);
+  launch_resid<MT, VT>(R.s, L, vals, r, cur, t, R.skip, h->dev_flags, h->stages);
   R.add(row_pass(L, sv) + 3.0 * sx * n);
   rec_child<VT>(R, k, t, cur);
   // post-smoothing
@@ -493,11 +564,11 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out) {
   for (int sw = 0; sw < post; ++sw) {
     VT* nxt = cur == za ? zb : za;
     if (sw == post - 1 && final_out) {
-      launch_sweep<MT, VT, double>(R.s, L, vals, dinv, r, cur, final_out, R.skip);
+      launch_sweep<MT, VT, double>(R.s, L, vals, dinv, r, cur, final_out, R.skip, h->dev_flags, h->stages);
       R.add(row_pass(L, sv) + 3.0 * sx * n + 8.0 * n);
       return nullptr;
     }
-    launch_sweep<MT, VT, VT>(R.s, L, vals, dinv, r, cur, nxt, R.skip);
+    launch_sweep<MT, VT, VT>(R.s, L, vals, dinv, r, cur, nxt, R.skip, h->dev_flags, h->stages);
     R.add(row_pass(L, sv) + 4.0 * sx * n);
     cur = nxt;
   }
@@ -534,14 +605,12 @@ static void record_iteration(VRec& R, bool precond) {
     k_copy<double, double><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, h->r, h->w, skip);
     R.add(16.0 * L.n);
   }
-  DISPATCH_R(L.Rd, (k_fcg_spmv_dots<TR><<<g, TR, 0, R.s>>>(L.n, L.rp, L.ci, L.v, h->w, h->r, h->q, h->v, st,
-                                                          h->partial, h->counter)));
+  launch_dots(h, R.s);
   R.add(bytes_spmv_dots(L));
   k_fcg_axpy<<<h->ax_grid, AMG_BLOCK, 0, R.s>>>(L.n, h->w, h->v, h->d, h->q, h->u, h->r, st, h->partial, h->counter);
   R.add(bytes_axpy(L));
   // the true-residual check moves data only once per solve (at convergence)
-  DISPATCH_R(L.Rd, (k_fcg_resid<TR, RES_TRUE><<<g, TR, 0, R.s>>>(L.n, L.rp, L.ci, L.v, h->b, h->u, h->r, st,
-                                                                 h->partial, h->counter)));
+  launch_fcg_resid<RES_TRUE>(h, R.s);
   R.add(0.0);
 }
 
@@ -593,7 +662,7 @@ amg_status amg_prepare_solve(amg_handle* h) {
   const int64_t tiles = (n + h->L[0].Rd - 1) / h->L[0].Rd;
   h->red_grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 8));
   h->ax_grid = (int)std::max<int64_t>(1, std::min<int64_t>(amg_blocks(n), (int64_t)sms * 8));
-  AMG_ALLOC(h, h->partial, double, (size_t)std::max(h->red_grid, h->ax_grid) * 4);
+  AMG_ALLOC(h, h->partial, double, (size_t)std::max(std::max(h->red_grid, h->ax_grid), 8192) * 4);
   AMG_ALLOC(h, h->counter, unsigned, 4);
   AMG_ALLOC(h, h->st, FcgState, 1);
   AMG_CK(h, cudaMallocHost((void**)&h->st_host, sizeof(FcgState)));
@@ -651,6 +720,17 @@ void amg_release_graphs(amg_handle* h) {
 // ---------------------------------------------------------------------------
 // solves
 
+// error bits raised by bounded device waits during the solve phase
+static amg_status check_device_flags(amg_handle* h) {
+  int f = 0;
+  AMG_CK(h, cudaMemcpyAsync(&f, h->dev_flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  AMG_CK(h, cudaStreamSynchronize(h->stream));
+  if (!f) return AMG_OK;
+  AMG_CK(h, cudaMemsetAsync(h->dev_flags, 0, sizeof(int), h->stream));
+  if (f & ST_TIMEOUT) return amg_fail(h, AMG_ERR_TIMEOUT, "a bounded wait of a row kernel expired");
+  return amg_fail(h, AMG_ERR_CUDA, "device error flags %d", f);
+}
+
 static amg_status ensure_hist(amg_handle* h, int maxit) {
   if (maxit + 1 <= h->hist_cap) return AMG_OK;
   if (h->hist) amg_release(h, h->hist);
@@ -679,8 +759,7 @@ static amg_status run_fcg(amg_handle* h, bool precond, double tol, int maxit, in
   hs->hist_len = maxit + 1;
   AMG_CK(h, cudaMemcpyAsync(h->st, hs, sizeof(FcgState), cudaMemcpyHostToDevice, s));
   const int g = h->red_grid;
-  DISPATCH_R(L.Rd, (k_fcg_resid<TR, RES_INIT><<<g, TR, 0, s>>>(n, L.rp, L.ci, L.v, h->b, h->u, h->r, h->st,
-                                                               h->partial, h->counter)));
+  launch_fcg_resid<RES_INIT>(h, s);
   AMG_CK(h, cudaGetLastError());
   AMG_CK(h, cudaMemcpyAsync(hs, h->st, sizeof(FcgState), cudaMemcpyDeviceToHost, s));
   AMG_CK(h, cudaStreamSynchronize(s));
@@ -700,11 +779,12 @@ static amg_status run_fcg(amg_handle* h, bool precond, double tol, int maxit, in
     AMG_CK(h, cudaStreamSynchronize(s));
   }
   if (hs->status != AMG_OK && hs->nb > 0.0) {
-    DISPATCH_R(L.Rd, (k_fcg_resid<TR, RES_NORM><<<g, TR, 0, s>>>(n, L.rp, L.ci, L.v, h->b, h->u, nullptr, h->st,
-                                                                 h->partial, h->counter)));
+    launch_fcg_resid<RES_NORM>(h, s);
     AMG_CK(h, cudaMemcpyAsync(hs, h->st, sizeof(FcgState), cudaMemcpyDeviceToHost, s));
     AMG_CK(h, cudaStreamSynchronize(s));
   }
+  amg_status fl = check_device_flags(h);
+  if (fl != AMG_OK) return fl;
   if (iters) *iters = hs->it;
   if (true_rel_res) *true_rel_res = hs->true_res;
   if (res_hist) {
@@ -765,7 +845,7 @@ extern "C" amg_status amg_vcycle(amg_handle* h, const double* r, double* z) {
   if (st != AMG_OK) return st;
   AMG_CK(h, cudaMemcpyAsync(z, h->w, bytes, cudaMemcpyDeviceToDevice, h->stream));
   AMG_CK(h, cudaStreamSynchronize(h->stream));
-  return AMG_OK;
+  return check_device_flags(h);
 }
 
 extern "C" amg_status amg_spmv(amg_handle* h, int32_t level, const double* x, double* y) {
@@ -816,16 +896,16 @@ static amg_status launch_one(amg_handle* h, int which, int k) {
     case 1:  // residual
       if (!L.lowp) {
         const double* r = k == 0 ? h->r : (const double*)L.r;
-        if (which == 0) launch_sweep<double, double, double>(s, L, L.v, L.dinv, r, (double*)L.za, (double*)L.zb, skip);
-        else launch_resid<double, double>(s, L, L.v, r, (double*)L.za, (double*)L.t, skip);
+        if (which == 0) launch_sweep<double, double, double>(s, L, L.v, L.dinv, r, (double*)L.za, (double*)L.zb, skip, h->dev_flags, h->stages);
+        else launch_resid<double, double>(s, L, L.v, r, (double*)L.za, (double*)L.t, skip, h->dev_flags, h->stages);
       } else {
         const float* r = k == 0 ? L.r0f : (const float*)L.r;
         if (L.vb) {
-          if (which == 0) launch_sweep<bf16, float, float>(s, L, L.vb, L.dinvf, r, (float*)L.za, (float*)L.zb, skip);
-          else launch_resid<bf16, float>(s, L, L.vb, r, (float*)L.za, (float*)L.t, skip);
+          if (which == 0) launch_sweep<bf16, float, float>(s, L, L.vb, L.dinvf, r, (float*)L.za, (float*)L.zb, skip, h->dev_flags, h->stages);
+          else launch_resid<bf16, float>(s, L, L.vb, r, (float*)L.za, (float*)L.t, skip, h->dev_flags, h->stages);
         } else {
-          if (which == 0) launch_sweep<float, float, float>(s, L, L.vf, L.dinvf, r, (float*)L.za, (float*)L.zb, skip);
-          else launch_resid<float, float>(s, L, L.vf, r, (float*)L.za, (float*)L.t, skip);
+          if (which == 0) launch_sweep<float, float, float>(s, L, L.vf, L.dinvf, r, (float*)L.za, (float*)L.zb, skip, h->dev_flags, h->stages);
+          else launch_resid<float, float>(s, L, L.vf, r, (float*)L.za, (float*)L.t, skip, h->dev_flags, h->stages);
         }
       }
       break;
@@ -847,8 +927,7 @@ static amg_status launch_one(amg_handle* h, int which, int k) {
     }
     case 4:
       if (k != 0) return amg_fail(h, AMG_ERR_INVALID_ARG, "outer kernels run on level 0");
-      DISPATCH_R(L.Rd, (k_fcg_spmv_dots<TR><<<g, TR, 0, s>>>(L.n, L.rp, L.ci, L.v, h->w, h->r, h->q, h->v, h->st,
-                                                            h->partial, h->counter)));
+      launch_dots(h, s);
       break;
     case 5:
       if (k != 0) return amg_fail(h, AMG_ERR_INVALID_ARG, "outer kernels run on level 0");
