@@ -153,6 +153,27 @@ amg_status amg_time_kernel(amg_handle* h, int32_t which, int32_t level, int32_t 
 /* bytes: host double; the algorithmic bytes of one launch of `which` on `level`
  * (values, column indices, row pointers and vector entries each counted once). */
 amg_status amg_kernel_bytes(const amg_handle* h, int32_t which, int32_t level, double* bytes);
+/*
+ * Residual check that allocates nothing (the paper has no counterpart; this is
+ * an addition of the library).  For callers that may not call cudaMalloc or
+ * cudaFree themselves, such as a component whose host owns all device memory
+ * through its own allocator, or a loop that cannot afford the synchronisation
+ * an allocation may cause.  Computes norms[0] = |b - A x|_2 and
+ * norms[1] = |b|_2, and r = b - A x when r is not NULL.
+ * A: device CSR (as for amg_setup; symmetry is not needed).  b, x: device, n.
+ * r: device, n, or NULL.  norms: device, 2 doubles.  stream: a cudaStream_t.
+ * The work is only enqueued: results are ready once the stream reaches it.
+ * Scratch space is a fixed device array inside the library (about 128 KB per
+ * GPU, held until the process exits), which bounds n to 2,097,152 rows; larger
+ * n returns AMG_ERR_TOO_LARGE.  The first call on a device looks up the array's
+ * address; make that first call before any stream capture.  Every call reuses
+ * the same array: calls whose work overlaps on the GPU race and give wrong
+ * results.  Errors: AMG_ERR_INVALID_ARG, AMG_ERR_TOO_LARGE, AMG_ERR_CUDA;
+ * amg_last_error(NULL) describes them.
+ */
+amg_status amg_residual_norm_noalloc(const amg_csr* A, const double* b, const double* x, double* r,
+                                     double* norms, void* stream);
+
 /* Last error message of the handle (or of the last failed amg_setup if h is NULL). */
 const char* amg_last_error(const amg_handle* h);
 

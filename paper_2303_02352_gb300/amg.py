@@ -80,6 +80,7 @@ def load(path: str | None = None):
         "amg_time_vcycle": (I32, [P, I32, DP]),
         "amg_time_kernel": (I32, [P, I32, I32, I32, DP]),
         "amg_kernel_bytes": (I32, [P, I32, I32, DP]),
+        "amg_residual_norm_noalloc": (I32, [ctypes.POINTER(amg_csr), P, P, P, P, P]),
         "amg_last_error": (ctypes.c_char_p, [P]),
         "amg_destroy": (None, [P]),
     }
