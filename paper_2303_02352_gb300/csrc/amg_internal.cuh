@@ -137,10 +137,15 @@ void amg_release(amg_handle* h, void* p);     // frees one allocation of the han
 
 static inline int amg_blocks(int64_t threads) { return (int)((threads + AMG_BLOCK - 1) / AMG_BLOCK); }
 
+// bytes of one pipeline stage of the row kernels (values + column indices)
+__host__ __device__ constexpr int amg_pipe_tile_bytes(int value_bytes) {
+  return value_bytes >= 8 ? 24576 : (value_bytes >= 4 ? 16384 : 12288);
+}
+
 // tile height of the row kernels: the largest of 256, 128, 64, 32 rows whose
-// longest-row bound fits the shared-memory tile (24 KB of values + indices)
+// longest-row bound fits one pipeline stage
 static inline int amg_tile_rows(int maxrow, int value_bytes) {
-  const int cap = 24576 / (value_bytes + 4);
+  const int cap = amg_pipe_tile_bytes(value_bytes) / (value_bytes + 4);
   int R = 256;
   while (R > 32 && (int64_t)R * maxrow > cap) R /= 2;
   return R;

@@ -1,13 +1,14 @@
 // Persistent TMA-pipelined row kernels (included by solve.cu).
 //
 // A block owns tiles of R consecutive rows, round-robin over the grid.  The
-// nonzeros of a tile are contiguous in CSR; one thread issues two 1D bulk
-// tensor copies (cp.async.bulk, the TMA engine) that move the tile's values and
-// column indices into a shared-memory stage and signal an mbarrier.  S stages
-// rotate: while the block computes tile k, the copies of tiles k+1 .. k+S-1 are
-// in flight, so HBM sees a continuous stream.  Each thread finishes one row
-// (one multiply-add per nonzero, no shuffle reduction: FP64 issue rate is a
-// co-limit on this part) and gathers the vector through L1/L2.
+// nonzeros of a tile are contiguous in CSR; a producer warp issues two 1D bulk
+// copies (cp.async.bulk, the TMA engine) that move the tile's values and column
+// indices into a shared-memory stage and signal the stage's "full" mbarrier.
+// S stages rotate: while the consumer warps compute tile k, the copies of the
+// next tiles are in flight, so HBM sees a continuous stream.  Each consumer
+// thread finishes one row (one multiply-add per nonzero, no shuffle reduction:
+// the FP64 issue rate is a co-limit on this part) and gathers the vector
+// through L1/L2.
 //
 // Every mbarrier wait is bounded; on expiry the kernel sets ST_TIMEOUT in the
 // device flags, drains its copies with a bounded wait and ends its tile loop.
@@ -15,13 +16,15 @@
 
 #include "amg_internal.cuh"
 
-#define PIPE_TILE_BYTES 24576
 #define PIPE_WAIT_LIMIT (1u << 22)
 
+// stage capacity (values + column indices): sized per value type so that a
+// 256-row tile of a 7-point stencil fits with little slack (smaller stages mean
+// more resident blocks per multiprocessor, which is what the row kernels need)
 template <typename MT>
 struct PipeTile {
   static constexpr int VE = 16 / (int)sizeof(MT);
-  static constexpr int CAP = PIPE_TILE_BYTES / ((int)sizeof(MT) + 4);
+  static constexpr int CAP = amg_pipe_tile_bytes((int)sizeof(MT)) / ((int)sizeof(MT) + 4);
   MT v[CAP + 2 * VE];
   int32_t c[CAP + 8];
 };
@@ -29,7 +32,8 @@ struct PipeTile {
 template <typename MT, int S>
 struct PipeSmem {
   PipeTile<MT> st[S];
-  unsigned long long bar[S];
+  unsigned long long full[S];   // producer -> consumers: the stage holds the tile
+  unsigned long long empty[S];  // consumers -> producer: every consumer warp has read it
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -93,8 +97,24 @@ struct RowArgs {
   int* flags;
 };
 
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// warp-uniform bounded wait (lane 0 polls, the result is broadcast)
+__device__ __forceinline__ bool mbar_wait_warp(unsigned long long* bar, uint32_t parity) {
+  bool ok = false;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity);
+  return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+
+// Warp-specialised persistent row kernel: R/32 consumer warps (one row per
+// thread) and one producer warp.  Per stage a "full" barrier (the producer's
+// expect_tx plus the bytes of the two bulk copies) and an "empty" barrier (one
+// arrival per consumer warp once it has read the stage).  No block-wide
+// barrier inside the tile loop: warps drift up to S tiles apart.
 template <int R, int S, int MODE, typename MT, typename VT, typename OT>
-__global__ void __launch_bounds__(R) k_rows_pipe(const RowArgs<MT, VT, OT> a) {
+__global__ void __launch_bounds__(R + 32) k_rows_pipe(const RowArgs<MT, VT, OT> a) {
   if constexpr (MODE == PM_SWEEP || MODE == PM_RESID) {
     if (*a.skip) return;
   } else if constexpr (MODE == PM_DOTS) {
@@ -106,100 +126,115 @@ __global__ void __launch_bounds__(R) k_rows_pipe(const RowArgs<MT, VT, OT> a) {
   auto* P = reinterpret_cast<PipeSmem<MT, S>*>(smem_raw);
   __shared__ double red[96];
   constexpr int VE = PipeTile<MT>::VE;
+  constexpr int NCW = R / 32;  // consumer warps
   const int n = a.n;
   const int ntiles = (n + R - 1) / R;
   const int G = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) mbar_init(&P->bar[s], 1);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&P->full[s], 1);
+      mbar_init(&P->empty[s], NCW);
+    }
     mbar_fence_init();
   }
   __syncthreads();
 
-  auto issue = [&](int k, int stage) {  // thread 0: copies of this block's k-th tile
-    const int tile = blockIdx.x + k * G;
-    if (tile >= ntiles) return;
-    const int row0 = tile * R, row1 = min(row0 + R, n);
-    const int p0 = __ldg(&a.rp[row0]), p1 = __ldg(&a.rp[row1]);
-    const int av = p0 & ~(VE - 1), ac = p0 & ~3;
-    const uint32_t bv = (uint32_t)(((p1 - av) * (int)sizeof(MT) + 15) & ~15);
-    const uint32_t bc = (uint32_t)(((p1 - ac) * 4 + 15) & ~15);
-    mbar_expect_tx(&P->bar[stage], bv + bc);
-    tma_load_1d(P->st[stage].v, a.v + av, bv, &P->bar[stage]);
-    tma_load_1d(P->st[stage].c, a.ci + ac, bc, &P->bar[stage]);
-  };
-  if (threadIdx.x == 0)
-    for (int k = 0; k < S; ++k) issue(k, k);
-
   double acc[3] = {0.0, 0.0, 0.0};
   const bool first = (MODE == PM_DOTS) ? (a.st->it == 0) : false;
-  int k = 0;
-  for (;; ++k) {
-    const int tile = blockIdx.x + k * G;
-    if (tile >= ntiles) break;
-    const int stage = k % S;
-    const uint32_t parity = (uint32_t)((k / S) & 1);
-    const int row0 = tile * R, row1 = min(row0 + R, n);
-    const int row = row0 + (int)threadIdx.x;
-    const bool live = row < row1;
-    const int p0 = __ldg(&a.rp[row0]);
-    int q0 = 0, q1 = 0;
-    VT own = 0, rr = 0, dd = 0, qq = 0;
-    if (live) {
-      q0 = __ldg(&a.rp[row]);
-      q1 = __ldg(&a.rp[row + 1]);
-      if constexpr (MODE == PM_SWEEP) {
-        own = __ldg(&a.x[row]);
-        rr = __ldg(&a.r[row]);
-        dd = __ldg(&a.dinv[row]);
-      } else if constexpr (MODE == PM_RESID) {
-        rr = __ldg(&a.r[row]);
-      } else if constexpr (MODE == PM_DOTS) {
-        own = __ldg(&a.x[row]);
-        rr = __ldg(&a.r[row]);
-        if (!first) qq = __ldg(&a.q[row]);
-      } else if constexpr (MODE == PM_RINIT || MODE == PM_RTRUE || MODE == PM_RNORM) {
-        rr = __ldg(&a.b[row]);
+
+  if (warp == NCW) {
+    // ---------------- producer warp ----------------
+    if (lane == 0) {
+      int k = 0;
+      bool aborted = false;
+      for (;; ++k) {
+        const int tile = blockIdx.x + k * G;
+        if (tile >= ntiles) break;
+        const int stage = k % S;
+        if (k >= S && !mbar_wait(&P->empty[stage], (uint32_t)(((k / S) - 1) & 1))) {
+          atomicOr(a.flags, ST_TIMEOUT);
+          aborted = true;
+          break;
+        }
+        const int row0 = tile * R, row1 = min(row0 + R, n);
+        const int p0 = __ldg(&a.rp[row0]), p1 = __ldg(&a.rp[row1]);
+        const int av = p0 & ~(VE - 1), ac = p0 & ~3;
+        const uint32_t bv = (uint32_t)(((p1 - av) * (int)sizeof(MT) + 15) & ~15);
+        const uint32_t bc = (uint32_t)(((p1 - ac) * 4 + 15) & ~15);
+        mbar_expect_tx(&P->full[stage], bv + bc);
+        tma_load_1d(P->st[stage].v, a.v + av, bv, &P->full[stage]);
+        tma_load_1d(P->st[stage].c, a.ci + ac, bc, &P->full[stage]);
       }
-    }
-    const bool ok = mbar_wait(&P->bar[stage], parity);
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) {
-        atomicOr(a.flags, ST_TIMEOUT);
-        for (int j = 0; j < S; ++j) {  // drain the copies this block may still have in flight
-          const int kk = k + j;
-          if (blockIdx.x + kk * G < ntiles) mbar_wait(&P->bar[kk % S], (uint32_t)((kk / S) & 1));
+      if (aborted) {  // drain: the last copy issued into each stage, bounded
+        for (int j = 1; j <= S && k - j >= 0; ++j) {
+          const int kk = k - j;
+          mbar_wait(&P->full[kk % S], (uint32_t)((kk / S) & 1));
         }
       }
-      __syncthreads();
-      break;
     }
-    const int av = p0 & ~(VE - 1), ac = p0 & ~3;
-    const PipeTile<MT>& T = P->st[stage];
-    VT s = 0;
+    __syncwarp();  // reconverge before the block-wide reduction below
+  } else {
+    // ---------------- consumer warps ----------------
+    for (int k = 0;; ++k) {
+      const int tile = blockIdx.x + k * G;
+      if (tile >= ntiles) break;
+      const int stage = k % S;
+      const int row0 = tile * R, row1 = min(row0 + R, n);
+      const int row = row0 + (int)threadIdx.x;
+      const bool live = row < row1;
+      const int p0 = __ldg(&a.rp[row0]);
+      int q0 = 0, q1 = 0;
+      VT own = 0, rr = 0, dd = 0, qq = 0;
+      if (live) {
+        q0 = __ldg(&a.rp[row]);
+        q1 = __ldg(&a.rp[row + 1]);
+        if constexpr (MODE == PM_SWEEP) {
+          own = __ldg(&a.x[row]);
+          rr = __ldg(&a.r[row]);
+          dd = __ldg(&a.dinv[row]);
+        } else if constexpr (MODE == PM_RESID) {
+          rr = __ldg(&a.r[row]);
+        } else if constexpr (MODE == PM_DOTS) {
+          own = __ldg(&a.x[row]);
+          rr = __ldg(&a.r[row]);
+          if (!first) qq = __ldg(&a.q[row]);
+        } else if constexpr (MODE == PM_RINIT || MODE == PM_RTRUE || MODE == PM_RNORM) {
+          rr = __ldg(&a.b[row]);
+        }
+      }
+      if (!mbar_wait_warp(&P->full[stage], (uint32_t)((k / S) & 1))) {
+        if (lane == 0) atomicOr(a.flags, ST_TIMEOUT);
+        break;
+      }
+      const int av = p0 & ~(VE - 1), ac = p0 & ~3;
+      const PipeTile<MT>& T = P->st[stage];
+      VT s = 0;
 #pragma unroll 8
-    for (int q = q0; q < q1; ++q) s += (VT)to_acc(T.v[q - av]) * __ldg(&a.x[T.c[q - ac]]);
-    if (live) {
-      if constexpr (MODE == PM_SWEEP) {
-        a.out[row] = (OT)(own + dd * (rr - s));
-      } else if constexpr (MODE == PM_RESID) {
-        a.out[row] = (OT)(rr - s);
-      } else if constexpr (MODE == PM_SPMV) {
-        a.out[row] = (OT)s;
-      } else if constexpr (MODE == PM_DOTS) {
-        a.out[row] = (OT)s;
-        acc[0] += (double)own * (double)rr;
-        acc[1] += (double)own * (double)s;
-        if (!first) acc[2] += (double)own * (double)qq;
-      } else {
-        const double ri = (double)rr - (double)s;
-        if constexpr (MODE != PM_RNORM) a.out[row] = (OT)ri;
-        acc[0] += ri * ri;
-        if constexpr (MODE == PM_RINIT) acc[1] += (double)rr * (double)rr;
+      for (int q = q0; q < q1; ++q) s += (VT)to_acc(T.v[q - av]) * __ldg(&a.x[T.c[q - ac]]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&P->empty[stage]);  // this warp is done with the stage
+      if (live) {
+        if constexpr (MODE == PM_SWEEP) {
+          a.out[row] = (OT)(own + dd * (rr - s));
+        } else if constexpr (MODE == PM_RESID) {
+          a.out[row] = (OT)(rr - s);
+        } else if constexpr (MODE == PM_SPMV) {
+          a.out[row] = (OT)s;
+        } else if constexpr (MODE == PM_DOTS) {
+          a.out[row] = (OT)s;
+          acc[0] += (double)own * (double)rr;
+          acc[1] += (double)own * (double)s;
+          if (!first) acc[2] += (double)own * (double)qq;
+        } else {
+          const double ri = (double)rr - (double)s;
+          if constexpr (MODE != PM_RNORM) a.out[row] = (OT)ri;
+          acc[0] += ri * ri;
+          if constexpr (MODE == PM_RINIT) acc[1] += (double)rr * (double)rr;
+        }
       }
     }
-    __syncthreads();  // every thread is done with this stage
-    if (threadIdx.x == 0) issue(k + S, stage);
   }
 
   if constexpr (MODE == PM_DOTS) {
@@ -241,7 +276,7 @@ static int pipe_grid(int n) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, R, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, R + 32, smem);
     bps = b < 1 ? 1 : b;
   }
   const int ntiles = (n + R - 1) / R;
@@ -253,5 +288,5 @@ template <int R, int S, int MODE, typename MT, typename VT, typename OT>
 static void launch_pipe(cudaStream_t s, const RowArgs<MT, VT, OT>& a) {
   const int grid = pipe_grid<R, S, MODE, MT, VT, OT>(a.n);
   constexpr int smem = (int)sizeof(PipeSmem<MT, S>);
-  k_rows_pipe<R, S, MODE, MT, VT, OT><<<grid, R, smem, s>>>(a);
+  k_rows_pipe<R, S, MODE, MT, VT, OT><<<grid, R + 32, smem, s>>>(a);
 }

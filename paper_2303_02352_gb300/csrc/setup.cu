@@ -745,8 +745,8 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
     const int vb = L.lowp ? ((h->p.precision == AMG_FP32_BF16FINE && k == 0) ? 2 : 4) : 8;
     L.Rd = amg_tile_rows(mr, 8);
     L.R = amg_tile_rows(mr, vb);
-    L.piped = h->use_pipe && (int64_t)L.Rd * mr <= 24576 / 12;
-    L.pipe = h->use_pipe && (int64_t)L.R * mr <= 24576 / (vb + 4);
+    L.piped = h->use_pipe && (int64_t)L.Rd * mr <= amg_pipe_tile_bytes(8) / 12;
+    L.pipe = h->use_pipe && (int64_t)L.R * mr <= amg_pipe_tile_bytes(vb) / (vb + 4);
     AMG_ALLOC(h, L.l1, double, L.n);
     AMG_ALLOC(h, L.dinv, double, L.n);
     if (L.lowp) {
