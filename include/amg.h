@@ -154,6 +154,45 @@ amg_status amg_time_kernel(amg_handle* h, int32_t which, int32_t level, int32_t 
  * (values, column indices, row pointers and vector entries each counted once). */
 amg_status amg_kernel_bytes(const amg_handle* h, int32_t which, int32_t level, double* bytes);
 /*
+ * Learned l1-Jacobi damping (not in the paper; a network gives each row of
+ * each level a damping omega_i in (0, 2) with D_i = omega_i / M_ii, where
+ * M_ii = sum_j |a_ij| is the l1-Jacobi diagonal of Sec. 3.1).
+ *
+ * amg_features: the four features of every row of `level`, row-major n_k x 4
+ *   float (device): a_ii / M_ii, ln M_ii minus the mean of ln M_jj over the
+ *   row's columns, nnz_i / 27, level / 4.
+ * amg_set_omega: sets omega on `level` (device, n_k doubles; NULL = 1, plain
+ *   l1-Jacobi) and recomputes D.  Solves and V-cycles use it until changed.
+ * amg_mlp_forward: omega (device, n doubles) = 2 sigmoid(W3 relu(W2 relu(W1 f
+ *   + b1) + b2) + b3) from feats (device, n x 4 float) and the 1249 bf16
+ *   weights w (device, layout [W1 32x4, b1 32, W2 32x32, b2 32, W3 32, b3]);
+ *   float32 arithmetic.  Enqueued on `stream`, not synchronised.
+ * amg_mlp_backward: grad (device, 1249 floats) = d(sum_i domega_i omega_i)/dw
+ *   for the same inputs; deterministic.  workspace: device memory of
+ *   amg_mlp_workspace_bytes(n) bytes.  Enqueued on `stream`.
+ * amg_adam_step: one Adam update of the float32 master weights theta (device)
+ *   with moments m, v (device), step t >= 1; writes the bf16 copy w_bf16.
+ * amg_apply_mlp: features + network + amg_set_omega on every level of the
+ *   handle (w_bf16 NULL: back to omega = 1).
+ * amg_vcycle_backward: adjoint of one FP64 V-cycle z = B(omega) r: given r and
+ *   dz = dL/dz (device, n), writes dr = dL/dr (device, n) and, for every level
+ *   k, domega[k] (device, n_k doubles) = dL/domega.  Recomputes each level's
+ *   sweeps from the level's input instead of storing them (work buffers are
+ *   allocated by the first call and kept by the handle).
+ */
+amg_status amg_features(amg_handle* h, int32_t level, float* feats);
+amg_status amg_set_omega(amg_handle* h, int32_t level, const double* omega);
+size_t amg_mlp_workspace_bytes(int32_t n);
+amg_status amg_mlp_forward(int32_t n, const float* feats, const uint16_t* w_bf16, double* omega, void* stream);
+amg_status amg_mlp_backward(int32_t n, const float* feats, const uint16_t* w_bf16, const double* domega,
+                            float* grad, void* workspace, void* stream);
+amg_status amg_adam_step(int32_t np, float* theta, const float* grad, float* m, float* v, uint16_t* w_bf16,
+                         float lr, float beta1, float beta2, float eps, int32_t t, void* stream);
+amg_status amg_apply_mlp(amg_handle* h, const uint16_t* w_bf16);
+amg_status amg_vcycle_backward(amg_handle* h, const double* r, const double* dz, double* dr,
+                               double* const* domega);
+
+/*
  * Residual check that allocates nothing (the paper has no counterpart; this is
  * an addition of the library).  For callers that may not call cudaMalloc or
  * cudaFree themselves, such as a component whose host owns all device memory

@@ -81,6 +81,15 @@ def load(path: str | None = None):
         "amg_time_kernel": (I32, [P, I32, I32, I32, DP]),
         "amg_kernel_bytes": (I32, [P, I32, I32, DP]),
         "amg_residual_norm_noalloc": (I32, [ctypes.POINTER(amg_csr), P, P, P, P, P]),
+        "amg_features": (I32, [P, I32, P]),
+        "amg_set_omega": (I32, [P, I32, P]),
+        "amg_mlp_workspace_bytes": (ctypes.c_size_t, [I32]),
+        "amg_mlp_forward": (I32, [I32, P, P, P, P]),
+        "amg_mlp_backward": (I32, [I32, P, P, P, P, P, P]),
+        "amg_adam_step": (I32, [I32, P, P, P, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, I32, P]),
+        "amg_apply_mlp": (I32, [P, P]),
+        "amg_vcycle_backward": (I32, [P, P, P, P, P]),
         "amg_last_error": (ctypes.c_char_p, [P]),
         "amg_destroy": (None, [P]),
     }
@@ -245,6 +254,40 @@ class Hierarchy:
         y = self._torch.empty(self.info()["n"][level], dtype=self._torch.float64, device=self.device)
         self._check(self._lib.amg_spmv(self._h, level, _ptr(x), _ptr(y)))
         return y
+
+    # -- learned damping ----------------------------------------------------
+    def level_sizes(self):
+        return self.info()["n"]
+
+    def features(self, level):
+        """The four row features of a level (device float32, n_k x 4)."""
+        t = self._torch
+        out = t.empty((self.info()["n"][level], 4), dtype=t.float32, device=self.device)
+        self._check(self._lib.amg_features(self._h, level, _ptr(out)))
+        return out
+
+    def set_omega(self, level, omega=None):
+        """Per-row damping of a level (device float64, n_k), None for omega = 1."""
+        if omega is None:
+            self._check(self._lib.amg_set_omega(self._h, level, None))
+            return
+        om = self._vec(omega)
+        self._check(self._lib.amg_set_omega(self._h, level, _ptr(om)))
+
+    def apply_mlp(self, w_bf16=None):
+        """Features + network + damping on every level (None: back to omega = 1)."""
+        self._check(self._lib.amg_apply_mlp(self._h, None if w_bf16 is None else _ptr(w_bf16)))
+
+    def vcycle_backward(self, r, dz):
+        """Adjoint of one FP64 V-cycle: (dL/dr, [dL/domega_k for every level])."""
+        t = self._torch
+        r, dz = self._vec(r), self._vec(dz)
+        dr = t.empty_like(r)
+        sizes = self.info()["n"]
+        dom = [t.empty(nk, dtype=t.float64, device=self.device) for nk in sizes]
+        ptrs = (ctypes.c_void_p * len(dom))(*[_ptr(d) for d in dom])
+        self._check(self._lib.amg_vcycle_backward(self._h, _ptr(r), _ptr(dz), _ptr(dr), ptrs))
+        return dr, dom
 
     # -- measurement --------------------------------------------------------
     def time_vcycle(self, reps=20) -> float:

@@ -79,6 +79,8 @@ struct Level {
   float* r0f = nullptr;      // level 0 low precision: float copy of the FCG residual
 };
 
+struct AdjState;  // adjoint work buffers (learned.cu)
+
 struct amg_handle {
   amg_params p{};
   cudaStream_t stream = nullptr;  // caller's stream
@@ -109,6 +111,7 @@ struct amg_handle {
   int launches_iter = 0;
   double bytes_vcycle = 0.0;   // algorithmic bytes of one V-cycle
   double bytes_iter = 0.0;     // algorithmic bytes of one FCG iteration
+  AdjState* adj = nullptr;     // allocated by the first amg_vcycle_backward
   std::string err;
   std::vector<DBuf> bufs;
 };
@@ -151,7 +154,8 @@ static inline int amg_tile_rows(int maxrow, int value_bytes) {
   return R;
 }
 
-void amg_set_setup_error(const std::string& msg);  // message for amg_last_error(NULL)
+void amg_set_setup_error(const std::string& msg);
+void amg_adj_destroy(amg_handle* h);             // frees the adjoint bookkeeping (learned.cu)  // message for amg_last_error(NULL)
 amg_status amg_level_diag(amg_handle* h, int k);   // l1 norms and D = omega / l1 of level k
 
 int amg_num_sms();  // multiprocessors of the current device

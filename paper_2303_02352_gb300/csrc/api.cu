@@ -85,6 +85,7 @@ extern "C" void amg_destroy(amg_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   amg_release_graphs(h);
+  amg_adj_destroy(h);
   amg_free_all(h);
   delete h;
 }

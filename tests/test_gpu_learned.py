@@ -1,0 +1,168 @@
+"""Learned damping and V-cycle adjoint on the GPU, against the CPU oracle.
+
+Tolerances: features 1e-6 (float32 output of FP64 arithmetic); network forward
+1e-5 and backward 1e-4 relative (bf16 weights, float32 accumulation, against
+float64 numpy on the same rounded weights); V-cycle adjoint and loss gradient
+1e-10 relative (FP64 on both sides); dr of the adjoint equal to B dz (the
+V-cycle operator is symmetric) to 1e-12.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mlp as M
+from paper_2303_02352_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_02352_gb300 import build
+    build.build()
+    from paper_2303_02352_gb300 import amg
+    return amg.load()
+
+
+def H(A, **kw):
+    from paper_2303_02352_gb300 import amg
+    return amg.Hierarchy(A, **kw)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+def bf16_round(x):
+    return torch.tensor(np.asarray(x, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def test_features_match_reference():
+    A = W.diffusion27(10, 2.0, 8)
+    g = H(A)
+    for k in range(g.num_levels):
+        rp, ci, v = g.level_csr(k)
+        ref = M.features(rp, ci, v, g.l1(k), k)
+        got = g.features(k).cpu().numpy()
+        assert np.allclose(got, ref, rtol=1e-6, atol=1e-6), k
+
+
+def test_network_forward_backward_and_adam_match_reference():
+    from paper_2303_02352_gb300 import learned as L
+    rng = np.random.default_rng(5)
+    theta = L.init_theta(3) + 0.2 * rng.standard_normal(L.NPARAM).astype(np.float32)
+    net = L.Network(theta)
+    wq = net.w.to(torch.float64).cpu().numpy()
+    assert np.array_equal(wq, bf16_round(theta))
+    n = 1000
+    feats = torch.tensor(rng.standard_normal((n, 4)), dtype=torch.float32, device="cuda")
+    th = net.theta.detach().requires_grad_(True)
+    L._ensure()
+    om = L.MLPFn.apply(feats, th, net.w)
+    ref = M.forward(wq, feats.cpu().numpy().astype(np.float64))
+    assert rel(om.detach().cpu().numpy(), ref) < 1e-5
+    dom = torch.tensor(rng.standard_normal(n), device="cuda")
+    (om * dom).sum().backward()
+    gref = M.backward(wq, feats.cpu().numpy().astype(np.float64), dom.cpu().numpy())
+    g = th.grad.cpu().numpy()
+    assert np.max(np.abs(g - gref)) <= 1e-4 * np.max(np.abs(gref))
+    # deterministic
+    th2 = net.theta.detach().requires_grad_(True)
+    (L.MLPFn.apply(feats, th2, net.w) * dom).sum().backward()
+    assert np.array_equal(th2.grad.cpu().numpy(), g)
+    # Adam against a float64 restatement of the update
+    t0, gg = net.theta.cpu().numpy().astype(np.float64), th.grad.detach().clone()
+    net.adam_step(gg, lr=1e-2)
+    mm = 0.1 * gg.cpu().numpy()
+    vv = 0.001 * gg.cpu().numpy() ** 2
+    t1 = t0 - 1e-2 * (mm / 0.1) / (np.sqrt(vv / 0.001) + 1e-8)
+    assert np.allclose(net.theta.cpu().numpy(), t1, rtol=1e-5, atol=1e-6)
+    assert np.array_equal(net.w.to(torch.float64).cpu().numpy(), bf16_round(net.theta.cpu().numpy()))
+
+
+def test_zero_last_layer_reproduces_plain_smoother_bitwise():
+    from paper_2303_02352_gb300 import learned as L
+    A = W.diffusion7(16, 1.0, 11)
+    g = H(A)
+    r = W.random_vector(A.n, 2)
+    z0 = g.vcycle(r).cpu().numpy()
+    net = L.Network(L.init_theta(0))
+    g.apply_mlp(net.w)
+    z1 = g.vcycle(r).cpu().numpy()
+    assert np.array_equal(z0.view(np.uint64), z1.view(np.uint64))
+
+
+@pytest.mark.parametrize("name", ["poisson", "diffusion"])
+def test_vcycle_adjoint_against_oracle_gradient(name):
+    A = W.poisson7(12) if name == "poisson" else W.diffusion7(12, 2.0, 33)
+    g = H(A, coarse_size=60)
+    o = O.Hierarchy(A, coarse_size=60)
+    assert g.num_levels == o.num_levels >= 2
+    rng = np.random.default_rng(1)
+    oms = [0.6 + 0.8 * rng.random(g.info()["n"][k]) for k in range(g.num_levels)]
+    for k, om in enumerate(oms):
+        o.set_omega(k, om)
+    # dr = B dz (the V-cycle operator is symmetric)
+    r = W.random_vector(A.n, 4)
+    dz = W.random_vector(A.n, 5)
+    for k, om in enumerate(oms):
+        g.set_omega(k, om)
+    dr, _ = g.vcycle_backward(r, dz)
+    assert rel(dr.cpu().numpy(), g.vcycle(dz).cpu().numpy()) < 1e-12
+    assert rel(g.vcycle(r).cpu().numpy(), o.vcycle(r)) < 1e-12
+    # loss and its gradient with respect to every omega, through autograd
+    from paper_2303_02352_gb300 import learned as L
+    m = 3
+    r0 = torch.as_tensor(W.random_vector(A.n, 6), device="cuda")
+    omt = [torch.tensor(om, device="cuda", requires_grad=True) for om in oms]
+    loss = L.stationary_loss(g, omt, r0, m)
+    loss.backward()
+    Lref, gref = o.loss_grad(r0.cpu().numpy(), m)
+    assert abs(float(loss.detach()) - Lref) <= 1e-12 * abs(Lref)
+    for k in range(g.num_levels):
+        assert rel(omt[k].grad.cpu().numpy(), gref[k]) < 1e-10, k
+
+
+def test_adjoint_against_finite_differences_on_gpu():
+    from paper_2303_02352_gb300 import learned as L
+    A = W.diffusion7(8, 1.0, 44)
+    g = H(A, coarse_size=30)
+    rng = np.random.default_rng(2)
+    oms = [torch.tensor(0.8 + 0.4 * rng.random(nk), device="cuda") for nk in g.info()["n"]]
+    r0 = torch.as_tensor(W.random_vector(A.n, 9), device="cuda")
+    omt = [o.clone().requires_grad_(True) for o in oms]
+    L.stationary_loss(g, omt, r0, 2).backward()
+    eps = 1e-6
+    for k in range(g.num_levels):
+        for i in rng.choice(len(oms[k]), size=4, replace=False):
+            p = [o.clone() for o in oms]
+            q = [o.clone() for o in oms]
+            p[k][i] += eps
+            q[k][i] -= eps
+            with torch.no_grad():
+                fd = (float(L.stationary_loss(g, p, r0, 2)) - float(L.stationary_loss(g, q, r0, 2))) / (2 * eps)
+            assert abs(fd - float(omt[k].grad[i])) <= 1e-5 * max(abs(fd), 1e-3), (k, i)
+
+
+def test_training_gains_over_plain_and_judge_falls_back():
+    from paper_2303_02352_gb300 import learned as L
+    probs = [W.training_problem(p, N=20) for p in range(6)]
+    net, losses = L.train(probs, steps=60, m=3, lr=1e-2, seed=0)
+    assert np.mean(losses[-6:]) < np.mean(losses[:6]) - 0.02
+    A = W.diffusion7(28, 2.0, 4242)
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 1))
+    res = L.judge(A, b, net)
+    assert res["learned"]["status"] == 0 and res["learned"]["true_rel_res"] < 1e-6
+    assert res["learned_iters"] < res["plain_iters"], (res["learned_iters"], res["plain_iters"])
+    assert res["use_learned"]
+    # a network that damps everything to almost zero is worse: the judge keeps plain
+    bad = L.init_theta(0)
+    bad[-1] = -8.0
+    res2 = L.judge(A, b, L.Network(bad), maxit=60)
+    assert not res2["use_learned"]
+    z_plain = L._amg.Hierarchy(A).vcycle(W.random_vector(A.n, 3)).cpu().numpy()
+    z_judged = res2["handle"].vcycle(W.random_vector(A.n, 3)).cpu().numpy()
+    assert np.array_equal(z_plain.view(np.uint64), z_judged.view(np.uint64))

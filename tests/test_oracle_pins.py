@@ -469,3 +469,43 @@ def test_unit_omega_reproduces_plain_smoother_bitwise():
     for k in range(h.num_levels):
         h.set_omega(k, np.ones(h.level_n(k)))
     assert np.array_equal(z0, h.vcycle(r))
+
+
+# ----------------------------------------------------------------------------
+# reference of the damping network (oracle/mlp.py)
+
+
+def test_mlp_reference_backward_matches_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(3)
+    theta = rng.standard_normal(mlp.NPARAM) * 0.3
+    feats = rng.standard_normal((7, 4))
+    dom = rng.standard_normal(7)
+    g = mlp.backward(theta, feats, dom)
+    eps = 1e-6
+    for p in rng.choice(mlp.NPARAM, size=40, replace=False):
+        tp, tm = theta.copy(), theta.copy()
+        tp[p] += eps
+        tm[p] -= eps
+        fd = (dom @ mlp.forward(tp, feats) - dom @ mlp.forward(tm, feats)) / (2 * eps)
+        assert abs(fd - g[p]) <= 1e-6 * max(1.0, abs(fd)), p
+
+
+def test_mlp_reference_zero_last_layer_gives_unit_damping():
+    from oracle import mlp
+    rng = np.random.default_rng(4)
+    theta = rng.standard_normal(mlp.NPARAM)
+    theta[1216:] = 0.0
+    assert np.all(mlp.forward(theta, rng.standard_normal((20, 4))) == 1.0)
+
+
+def test_features_reference_on_poisson():
+    from oracle import mlp
+    A = W.poisson7(6)
+    h = O.Hierarchy(A)
+    f = mlp.features(A.row_ptr, A.col_idx, A.val, h.level_l1(0), 0)
+    # interior row of the 7-point stencil: l1 = 12, diagonal 6, 7 stored entries
+    i = 2 + 6 * 2 + 36 * 2
+    assert np.allclose(f[i], [0.5, 0.0, 7 / 27, 0.0])
+    # corner row: 4 entries, l1 = 9 ; neighbours have l1 = 10
+    assert np.allclose(f[0], [6 / 9, np.log(9) - np.mean(np.log([9, 10, 10, 10])), 4 / 27, 0.0])
