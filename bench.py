@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--precision", choices=list(PRECISIONS), default="fp64")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the low-precision comparison solves")
+    ap.add_argument("--learned", action="store_true", help="time the solve with the trained damping network")
+    ap.add_argument("--no-extra", action="store_true", help="skip the comparison solves of the other forms")
     return ap.parse_args()
 
 
@@ -194,7 +195,7 @@ def oracle_solve_ms(A, b, precision: str, maxit=1000):
     t1 = time.perf_counter()
     res = h.fcg(b, maxit=maxit)
     t2 = time.perf_counter()
-    return (t2 - t1) * 1e3, (t1 - t0) * 1e3, res["iters"], h
+    return (t2 - t1) * 1e3, (t1 - t0) * 1e3, res["iters"], res["x"]
 
 
 def run_reference(args, rank, world):
@@ -257,13 +258,23 @@ def main():
 
     # CPU baseline first (host only, rank 0, N = 1)
     cpu = None
+    x_oracle = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ms_o, setup_o, it_o, _ = oracle_solve_ms(A, b_np, args.precision)
+        ms_o, setup_o, it_o, x_oracle = oracle_solve_ms(A, b_np, "fp64")
         cpu = {"value": ms_o, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one complete oracle solve (serial C, {args.precision}) of {desc} to {args.tol:g}: "
+               "sample": f"one complete oracle solve (serial C, fp64) of {desc} to {args.tol:g}: "
                          f"{it_o} iterations; oracle setup {setup_o:.0f} ms not included"}
 
+    net = None
+    if args.learned or not args.no_extra:
+        from paper_2303_02352_gb300 import learned
+        if os.path.exists(learned.DEFAULT_WEIGHTS):
+            net = learned.Network.load()
+        elif args.learned:
+            raise SystemExit("--learned needs trained weights (python -m paper_2303_02352_gb300.train_omega)")
     g = amg.Hierarchy(A, precision=PRECISIONS[args.precision])
+    if args.learned:
+        g.apply_mlp(net.w)
     info = g.info()
     b = torch.as_tensor(b_np, dtype=torch.float64, device="cuda")
     x = torch.zeros_like(b)
@@ -332,35 +343,50 @@ def main():
     replays = -(-iters // batch) * batch if iters > 0 else 0
     launches_per_solve = 1 + replays * info["iteration_launches"]
 
-    extra = {}
-    if not args.no_extra and args.precision == "fp64":
-        for pname in ("fp32", "bf16fine"):
-            g2 = amg.Hierarchy(A, precision=PRECISIONS[pname])
-            x2 = torch.zeros_like(b)
-            for _ in range(2):
-                x2.zero_()
-                r2 = g2.solve_into(b, x2, args.tol, 1000)
-            torch.cuda.synchronize()
-            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            q0.record(stream)
-            for _ in range(args.steps):
-                x2.zero_()
-                r2 = g2.solve_into(b, x2, args.tol, 1000)
-            q1.record(stream)
-            torch.cuda.synchronize()
-            xd = x.double()
-            extra[pname] = {"ms": q0.elapsed_time(q1) / args.steps, "iters": r2["iters"],
-                            "true_rel_res": r2["true_rel_res"],
-                            "rel_diff_vs_fp64_solution": float((x2 - xd).norm() / xd.norm()),
-                            "vcycle_ms": g2.time_vcycle(reps=20), "vcycle_bytes": g2.info()["vcycle_bytes"]}
-            g2.close()
+    xs = torch.as_tensor(W.exact_solution(args.workload, n), device="cuda")
+    xo = torch.as_tensor(x_oracle, device="cuda") if x_oracle is not None else None
+
+    def errors(xv):
+        e = {}
+        if xo is not None:
+            e["rel_err_vs_fp64_oracle"] = float((xv - xo).norm() / xo.norm())
+        if xs is not None:
+            e["rel_err_vs_exact"] = float((xv - xs).norm() / xs.norm())
+        return e
+
+    head = {"ms": ms, "iters": iters, "true_rel_res": res["true_rel_res"], **errors(x)}
+    forms = {("%s%s" % (args.precision, "+learned" if args.learned else "")): head}
+    if not args.no_extra:
+        for pname in ("fp64", "fp32", "bf16fine"):
+            for use_net in (False, True):
+                key = pname + ("+learned" if use_net else "")
+                if key in forms or (use_net and net is None):
+                    continue
+                g2 = amg.Hierarchy(A, precision=PRECISIONS[pname])
+                if use_net:
+                    g2.apply_mlp(net.w)
+                x2 = torch.zeros_like(b)
+                for _ in range(2):
+                    r2 = g2.solve_into(b, x2.zero_(), args.tol, 1000)
+                torch.cuda.synchronize()
+                q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                q0.record(stream)
+                for _ in range(args.steps):
+                    r2 = g2.solve_into(b, x2.zero_(), args.tol, 1000)
+                q1.record(stream)
+                torch.cuda.synchronize()
+                forms[key] = {"ms": q0.elapsed_time(q1) / args.steps, "iters": r2["iters"],
+                              "true_rel_res": r2["true_rel_res"], **errors(x2),
+                              "vcycle_ms": g2.time_vcycle(reps=20), "vcycle_bytes": g2.info()["vcycle_bytes"]}
+                g2.close()
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": {"workload": desc, "precision": args.precision, "tol": args.tol,
+            "config": {"workload": desc, "precision": args.precision, "learned_damping": bool(args.learned),
+                       "tol": args.tol,
                        "replicas": world, "l2": "inputs larger than L2 (level-0 matrix %.0f MB)" % (A.nnz * 12 / 1e6),
                        "levels": info["num_levels"], "n": info["n"], "nnz": info["nnz"],
                        "opc": round(info["opc"], 4), "iters": iters},
@@ -378,7 +404,7 @@ def main():
             "gpu_launches": launches_per_solve * args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
-            "low_precision": extra or None,
+            "forms": forms,
         }
         print(json.dumps(line), flush=True)
     g.close()

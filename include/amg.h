@@ -213,6 +213,12 @@ amg_status amg_vcycle_backward(amg_handle* h, const double* r, const double* dz,
 amg_status amg_residual_norm_noalloc(const amg_csr* A, const double* b, const double* x, double* r,
                                      double* norms, void* stream);
 
+/* Self-check of the bounded device waits: launches one block that waits on a
+ * barrier phase nothing completes, with a limit of limit_us microseconds
+ * (1 .. 2,000,000).  Returns AMG_ERR_TIMEOUT when the wait gave up and
+ * reported as designed (the expected result), AMG_OK if it did not. */
+amg_status amg_check_bounded_wait(int32_t limit_us, void* stream);
+
 /* Last error message of the handle (or of the last failed amg_setup if h is NULL). */
 const char* amg_last_error(const amg_handle* h);
 

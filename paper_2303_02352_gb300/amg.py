@@ -81,6 +81,7 @@ def load(path: str | None = None):
         "amg_time_kernel": (I32, [P, I32, I32, I32, DP]),
         "amg_kernel_bytes": (I32, [P, I32, I32, DP]),
         "amg_residual_norm_noalloc": (I32, [ctypes.POINTER(amg_csr), P, P, P, P, P]),
+        "amg_check_bounded_wait": (I32, [I32, P]),
         "amg_features": (I32, [P, I32, P]),
         "amg_set_omega": (I32, [P, I32, P]),
         "amg_mlp_workspace_bytes": (ctypes.c_size_t, [I32]),

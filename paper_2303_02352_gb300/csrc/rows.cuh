@@ -10,13 +10,14 @@
 // the FP64 issue rate is a co-limit on this part) and gathers the vector
 // through L1/L2.
 //
-// Every mbarrier wait is bounded; on expiry the kernel sets ST_TIMEOUT in the
-// device flags, drains its copies with a bounded wait and ends its tile loop.
+// Every mbarrier wait is bounded in time (2 s); on expiry the kernel sets
+// ST_TIMEOUT in the device flags, drains its copies with a bounded wait and
+// ends its tile loop; the host maps the flag to AMG_ERR_TIMEOUT.
 #pragma once
 
 #include "amg_internal.cuh"
 
-#define PIPE_WAIT_LIMIT (1u << 22)
+#define PIPE_WAIT_NS 2000000000ull  // 2 s: a copy of at most 24 KB never takes this long
 
 // stage capacity (values + column indices): sized per value type so that a
 // 256-row tile of a 7-point stencil fits with little slack (smaller stages mean
@@ -69,11 +70,23 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t 
   return ok != 0;
 }
 
-// bounded wait: true when the phase completed
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < PIPE_WAIT_LIMIT; ++i)
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bounded wait: true when the phase completed, false after limit_ns of
+// polling (the clock is read every 64 polls, so the bound holds whatever the
+// suspend time of a single try_wait)
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity,
+                                          uint64_t limit_ns = PIPE_WAIT_NS) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-  return false;
+    if ((i & 63u) == 0u && global_ns() - t0 > limit_ns) return false;
+  }
 }
 
 enum { PM_SWEEP = 0, PM_RESID = 1, PM_SPMV = 2, PM_DOTS = 3, PM_RINIT = 4, PM_RTRUE = 5, PM_RNORM = 6 };

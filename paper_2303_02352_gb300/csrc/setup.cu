@@ -35,6 +35,7 @@ amg_status amg_fail(amg_handle* h, amg_status s, const char* fmt, ...) {
 void* amg_alloc(amg_handle* h, size_t bytes) {
   size_t sz = ((bytes + 255) / 256) * 256 + 256;
   void* p = nullptr;
+  if (h->fail_alloc_after >= 0 && h->n_allocs++ >= h->fail_alloc_after) return nullptr;  // test hook
   if (cudaMalloc(&p, sz) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
@@ -547,6 +548,7 @@ static amg_status pairwise_step(amg_handle* h, const PCsr& cur, int32_t* agg, in
   k_other_rank<<<nb, AMG_BLOCK, 0, s>>>(n, cur.rp, cur.ci, rank_of, srt_pos, cnt, srt_col, key_rank, h->dev_flags);
   AMG_CK(h, cudaMemsetAsync(suitor, 0xff, sizeof(unsigned long long) * (size_t)n, s));
   long long cap = 2 * (long long)nnz + (long long)n + 1024;
+  if (h->suitor_cap >= 0) cap = h->suitor_cap;  // test hook
   k_suitor<<<nb, AMG_BLOCK, 0, s>>>(n, cur.rp, cnt, srt_col, key_rank, suitor, next, cap, h->dev_flags);
   k_mate<<<nb, AMG_BLOCK, 0, s>>>(n, suitor, mate, opener);
   scan_exclusive(s, n, opener, pos, scratch, total);
@@ -779,6 +781,11 @@ extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* str
   if (p) h->p = *p;
   else amg_params_default(&h->p);
   h->stream = (cudaStream_t)stream;
+  // test and tuning hooks (environment): AMG_PIPE=0 non-pipelined row kernels,
+  // AMG_STAGES pipeline depth, AMG_SUITOR_CAP step cap of the matching loop,
+  // AMG_FAIL_ALLOC_AFTER make the k-th device allocation of the handle fail
+  if (const char* e = getenv("AMG_SUITOR_CAP")) h->suitor_cap = atoll(e);
+  if (const char* e = getenv("AMG_FAIL_ALLOC_AFTER")) h->fail_alloc_after = atoi(e);
   if (const char* e = getenv("AMG_PIPE")) h->use_pipe = atoi(e);
   if (const char* e = getenv("AMG_STAGES")) h->stages = atoi(e);
   amg_status st = setup_impl(h, A);

@@ -720,6 +720,32 @@ void amg_release_graphs(amg_handle* h) {
 // ---------------------------------------------------------------------------
 // solves
 
+// Self-check of the bounded-wait path: one block waits on an mbarrier phase
+// that nothing completes; the wait must give up after limit_us and report.
+__global__ void k_bounded_wait_check(uint64_t limit_ns, int* flags) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit_ns)) atomicOr(flags, ST_TIMEOUT);
+}
+
+extern "C" amg_status amg_check_bounded_wait(int32_t limit_us, void* stream) {
+  if (limit_us <= 0 || limit_us > 2000000) return AMG_ERR_INVALID_ARG;
+  int* flags = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMallocAsync((void**)&flags, sizeof(int), s) != cudaSuccess) return AMG_ERR_OOM;
+  int host = 0;
+  cudaMemsetAsync(flags, 0, sizeof(int), s);
+  k_bounded_wait_check<<<1, 32, 0, s>>>((uint64_t)limit_us * 1000ull, flags);
+  cudaMemcpyAsync(&host, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(flags, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
+  return (host & ST_TIMEOUT) ? AMG_ERR_TIMEOUT : AMG_OK;
+}
+
 // error bits raised by bounded device waits during the solve phase
 static amg_status check_device_flags(amg_handle* h) {
   int f = 0;

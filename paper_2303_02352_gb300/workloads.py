@@ -219,26 +219,34 @@ def training_problem(p: int, N: int = 64) -> CSR:
     return diffusion7(N, training_sigma(p), 1000 + p)
 
 
-def config(name: str):
-    """Named workloads.  Returns (A, b, description)."""
-    if name == "poisson32":
-        A = poisson7(32)
-        return A, rhs_from_solution(A, random_vector(A.n, 1)), "7-pt Poisson 32^3, b = A x*, x* ~ U(-1,1) seed 1"
-    if name == "poisson160":
-        A = poisson7(160)
-        return A, rhs_from_solution(A, random_vector(A.n, 2)), "7-pt Poisson 160^3, b = A x*, x* ~ U(-1,1) seed 2"
-    if name == "diffusion27_128":
-        A = diffusion27(128, 2.0, 3)
-        return A, rhs_from_solution(A, random_vector(A.n, 3)), "27-pt log-normal diffusion 128^3, sigma 2, seed 3"
-    if name == "diffusion7_256":
-        A = diffusion7(256, 2.0, 4000)
-        return A, rhs_from_solution(A, random_vector(A.n, 4)), "7-pt log-normal diffusion 256^3, sigma 2, seed 4000"
-    if name == "poisson320":
-        A = poisson7(320)
-        return A, rhs_from_solution(A, random_vector(A.n, 5)), "7-pt Poisson 320^3, b = A x*, x* ~ U(-1,1) seed 5"
+_CONFIGS = {
+    "poisson32": (lambda: poisson7(32), 1, "7-pt Poisson 32^3, b = A x*, x* ~ U(-1,1) seed 1"),
+    "poisson160": (lambda: poisson7(160), 2, "7-pt Poisson 160^3, b = A x*, x* ~ U(-1,1) seed 2"),
+    "diffusion27_128": (lambda: diffusion27(128, 2.0, 3), 3,
+                        "27-pt log-normal diffusion 128^3 (sigma 2, 8^3 blocks, seed 3), b = A x*, x* seed 3"),
+    "diffusion7_256": (lambda: diffusion7(256, 2.0, 4000), 4,
+                       "7-pt log-normal diffusion 256^3 (sigma 2, 8^3 blocks, seed 4000), b = A x*, x* seed 4"),
+    "poisson320": (lambda: poisson7(320), 5, "7-pt Poisson 320^3, b = A x*, x* ~ U(-1,1) seed 5"),
+}
+
+
+def _config_entry(name: str):
+    if name in _CONFIGS:
+        return _CONFIGS[name]
     m = __import__("re").fullmatch(r"poisson(\d+)", name)
     if m:
         N = int(m.group(1))
-        A = poisson7(N)
-        return A, rhs_from_solution(A, random_vector(A.n, N)), f"7-pt Poisson {N}^3, seed {N}"
+        return (lambda: poisson7(N)), N, f"7-pt Poisson {N}^3, b = A x*, x* ~ U(-1,1) seed {N}"
     raise KeyError(name)
+
+
+def config(name: str):
+    """Named workloads.  Returns (A, b, description); b = A x* with x* = exact_solution."""
+    gen, seed, desc = _config_entry(name)
+    A = gen()
+    return A, rhs_from_solution(A, random_vector(A.n, seed)), desc
+
+
+def exact_solution(name: str, n: int) -> np.ndarray:
+    """x* of a named workload (the solution of A x = b)."""
+    return random_vector(n, _config_entry(name)[1])
