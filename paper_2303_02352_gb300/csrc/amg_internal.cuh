@@ -104,6 +104,9 @@ struct amg_handle {
   int ax_grid = 0;             // grid of the fused axpys
   int stages = 2;              // pipeline depth of the row kernels (2 measured best: more stages cost resident blocks)
   int use_pipe = 1;            // 0: non-pipelined tiled row kernels
+  int use_bottom = 0;          // 1: bottom levels in one cluster launch (measured slower; off)
+  int small_rows = 0;          // levels with fewer rows use the non-pipelined tiled kernels
+  int kb = AMG_MAXL;           // first level of the fused bottom (nl: none)
   long long suitor_cap = -1;   // test hook: step cap of the matching loop (-1: proof-level bound)
   int fail_alloc_after = -1;   // test hook: the allocation with this index fails (-1: never)
   int n_allocs = 0;

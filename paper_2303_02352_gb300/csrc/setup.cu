@@ -747,8 +747,9 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
     const int vb = L.lowp ? ((h->p.precision == AMG_FP32_BF16FINE && k == 0) ? 2 : 4) : 8;
     L.Rd = amg_tile_rows(mr, 8);
     L.R = amg_tile_rows(mr, vb);
+    const bool big = L.n >= h->small_rows;
     L.piped = h->use_pipe && (int64_t)L.Rd * mr <= amg_pipe_tile_bytes(8) / 12;
-    L.pipe = h->use_pipe && (int64_t)L.R * mr <= amg_pipe_tile_bytes(vb) / (vb + 4);
+    L.pipe = h->use_pipe && big && (int64_t)L.R * mr <= amg_pipe_tile_bytes(vb) / (vb + 4);
     AMG_ALLOC(h, L.l1, double, L.n);
     AMG_ALLOC(h, L.dinv, double, L.n);
     if (L.lowp) {
@@ -766,6 +767,14 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
       if (st != AMG_OK) return st;
     }
   }
+  // fused bottom: the levels k >= 1 with at most 16384 rows (at most 8 of them)
+  h->kb = h->nl;
+  if (h->use_bottom)
+    for (int k = 1; k < h->nl; ++k)
+      if (h->L[k].n <= 16384 && h->nl - k <= 8) {
+        h->kb = k;
+        break;
+      }
   AMG_CK(h, cudaStreamSynchronize(s));
   AMG_CK(h, cudaGetLastError());
   return amg_prepare_solve(h);
@@ -782,9 +791,12 @@ extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* str
   else amg_params_default(&h->p);
   h->stream = (cudaStream_t)stream;
   // test and tuning hooks (environment): AMG_PIPE=0 non-pipelined row kernels,
-  // AMG_STAGES pipeline depth, AMG_SUITOR_CAP step cap of the matching loop,
+  // AMG_STAGES pipeline depth, AMG_BOTTOM=0 bottom levels as separate launches,
+  // AMG_SUITOR_CAP step cap of the matching loop,
   // AMG_FAIL_ALLOC_AFTER make the k-th device allocation of the handle fail
   if (const char* e = getenv("AMG_SUITOR_CAP")) h->suitor_cap = atoll(e);
+  if (const char* e = getenv("AMG_BOTTOM")) h->use_bottom = atoi(e);
+  if (const char* e = getenv("AMG_SMALL_ROWS")) h->small_rows = atoi(e);
   if (const char* e = getenv("AMG_FAIL_ALLOC_AFTER")) h->fail_alloc_after = atoi(e);
   if (const char* e = getenv("AMG_PIPE")) h->use_pipe = atoi(e);
   if (const char* e = getenv("AMG_STAGES")) h->stages = atoi(e);

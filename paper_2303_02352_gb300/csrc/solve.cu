@@ -348,6 +348,7 @@ int amg_num_sms() {
 }
 
 #include "rows.cuh"
+#include "bottom.cuh"
 
 // ---------------------------------------------------------------------------
 // launch helpers (dispatch on the tile height and on the pipeline depth)
@@ -480,6 +481,50 @@ static double* rec_coarse(VRec& R, int k, const double* r, double* final_out) {
 template <typename VT, typename MT, typename RT>
 static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out);
 
+// the bottom levels kb .. nl-1 in one cluster launch; result in L[kb].za
+static void rec_bottom(VRec& R) {
+  amg_handle* h = R.h;
+  const int kb = h->kb;
+  BotArgs a{};
+  a.nb = h->nl - kb;
+  a.pre = h->p.pre_sweeps;
+  a.post = h->p.post_sweeps;
+  a.csweeps = h->p.coarse_sweeps;
+  a.skip = R.skip;
+  double bytes = 0.0;
+  for (int j = 0; j < a.nb; ++j) {
+    Level& L = h->L[kb + j];
+    const bool coarsest = kb + j == h->nl - 1;
+    BotLevel& B = a.L[j];
+    B.n = L.n;
+    B.rp = L.rp;
+    B.ci = L.ci;
+    B.v = L.lowp ? (const void*)L.vf : (const void*)L.v;
+    B.dinv = L.lowp ? (const void*)L.dinvf : (const void*)L.dinv;
+    B.agg = coarsest ? nullptr : L.agg;
+    B.mptr = coarsest ? nullptr : L.mptr;
+    B.mem = coarsest ? nullptr : L.mem;
+    B.r = L.r;
+    B.za = L.za;
+    B.zb = L.zb;
+    B.t = L.t;
+    const double n = L.n, sx = vec_bytes(L), sv = val_bytes(L);
+    if (coarsest) {
+      bytes += 3.0 * sx * n + (h->p.coarse_sweeps - 1) * (row_pass(L, sv) + 4.0 * sx * n);
+    } else {
+      const Level& C = h->L[kb + j + 1];
+      const double nc = C.n, sc = vec_bytes(C);
+      bytes += 3.0 * sx * n + (h->p.pre_sweeps - 1 + h->p.post_sweeps) * (row_pass(L, sv) + 4.0 * sx * n);
+      bytes += row_pass(L, sv) + 3.0 * sx * n;                           // residual
+      bytes += 4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc;              // restriction
+      bytes += 4.0 * n + sc * nc + 2.0 * sx * n;                         // prolongation
+    }
+  }
+  if (h->L[kb].lowp) launch_bottom<float, float>(R.s, a);
+  else launch_bottom<double, double>(R.s, a);
+  R.add(bytes);
+}
+
 template <typename VT>
 static void rec_child(VRec& R, int k, const VT* t, VT* z) {
   amg_handle* h = R.h;
@@ -487,6 +532,22 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
   Level& C = h->L[k + 1];
   const int ncb = amg_blocks(C.n);
   const double sx = sizeof(VT), n = L.n, nc = C.n;
+  if (k + 1 == h->kb) {  // the bottom levels in one launch
+    const double sc = vec_bytes(C);
+    if (k + 1 == h->nl - 1) {
+      k_restrict<VT, double><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, L.mptr, L.mem, t, (double*)C.r, R.skip);
+      R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 8.0 * nc);
+      rec_bottom(R);
+      k_prolong<VT, double><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, L.agg, (const double*)C.za, z, R.skip);
+    } else {
+      k_restrict<VT, VT><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip);
+      R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc);
+      rec_bottom(R);
+      k_prolong<VT, VT><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, L.agg, (const VT*)C.za, z, R.skip);
+    }
+    R.add(4.0 * n + sc * nc + 2.0 * sx * n);
+    return;
+  }
   if (k + 1 == h->nl - 1) {  // coarsest: FP64
     k_restrict<VT, double><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, L.mptr, L.mem, t, (double*)C.r, R.skip);
     R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 8.0 * nc);

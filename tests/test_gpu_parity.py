@@ -290,3 +290,20 @@ def test_full_size_vcycle_and_solve(big):
     # the oracle's first two FCG iterates
     xg = g.pcg_solve(b, tol=0.0, maxit=2)["x"].cpu().numpy()
     assert rel(xg, o.fcg(b, tol=0.0, maxit=2)["x"]) < 1e-10
+
+
+@pytest.mark.parametrize("name", ["poisson16", "poisson32", "diff27_12"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_fused_bottom_matches_separate_launches(name, prec, monkeypatch):
+    A = PROBLEMS[name]()
+    r = W.random_vector(A.n, 12)
+    monkeypatch.setenv("AMG_BOTTOM", "0")
+    z0 = G(A, precision=prec).vcycle(r).cpu().numpy()
+    monkeypatch.setenv("AMG_BOTTOM", "1")
+    z1 = G(A, precision=prec).vcycle(r).cpu().numpy()
+    assert rel(z1, z0) < (1e-13 if prec == 0 else 1e-6)
+    # the non-pipelined tiled row kernels on every level
+    monkeypatch.setenv("AMG_BOTTOM", "0")
+    monkeypatch.setenv("AMG_SMALL_ROWS", "100000000")
+    z2 = G(A, precision=prec).vcycle(r).cpu().numpy()
+    assert rel(z2, z0) < (1e-13 if prec == 0 else 1e-6)
