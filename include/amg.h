@@ -69,6 +69,9 @@ typedef struct {
   int32_t true_res_every; /* low precision: r <- b - A u every k iterations (50); 0 = never */
   int32_t use_graph;      /* 1: replay the V-cycle and the FCG iteration as CUDA graphs (1) */
   int32_t graph_batch;    /* FCG iterations launched between two convergence reads (4) */
+  int32_t num_parts;      /* decoupled aggregation (Sec. 4.1): match only inside this many
+                             contiguous row blocks, as np tasks would (1 = global matching) */
+  int32_t cycle;          /* Listing 1 cycle_type: 0 V-cycle, 2 W-cycle (0) */
 } amg_params;
 
 typedef struct {
@@ -83,6 +86,8 @@ typedef struct {
   int32_t vcycle_launches;    /* kernel launches of one V-cycle */
   int32_t iteration_launches; /* kernel launches of one FCG iteration */
   int32_t precision;          /* amg_precision of the hierarchy */
+  double setup_match_ms;      /* setup time in the matching steps (weights, suitor, aggregation) */
+  double setup_galerkin_ms;   /* setup time in the Galerkin products */
 } amg_info_t;
 
 typedef struct amg_handle amg_handle;

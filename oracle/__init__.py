@@ -43,7 +43,7 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int) for name in (
         "aggr_steps", "max_levels", "coarse_size", "pre_sweeps", "post_sweeps",
-        "coarse_sweeps", "coarse_solver", "precision", "true_res_every")]
+        "coarse_sweeps", "coarse_solver", "precision", "true_res_every", "num_parts", "cycle")]
 
 
 def _lib():
@@ -144,6 +144,8 @@ class Params:
     coarse_solver: int = COARSE_L1JACOBI
     precision: int = FP64
     true_res_every: int = 50
+    num_parts: int = 1
+    cycle: int = 0
 
     def _c(self):
         p = _Params()

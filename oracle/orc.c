@@ -69,6 +69,8 @@ void orc_params_default(orc_params* p) {
   p->coarse_solver = ORC_COARSE_L1JACOBI;
   p->precision = ORC_FP64;
   p->true_res_every = 50;
+  p->num_parts = 1;
+  p->cycle = 0;
 }
 
 static void* xcalloc(size_t n, size_t s) {
@@ -112,6 +114,26 @@ int orc_weights(int n, const int32_t* rp, const int32_t* ci, const double* v, do
     }
   }
   free(diag);
+  return ORC_OK;
+}
+
+/* decoupled aggregation (Sec. 4.1): every task matches only its own rows, so
+ * an edge whose ends lie in different row blocks is not an edge */
+static int part_of(int i, int np, const int32_t* bnd) {
+  int p = 0;
+  while (p + 1 < np && i >= bnd[p + 1]) ++p;
+  return p;
+}
+
+int orc_weights_parts(int n, const int32_t* rp, const int32_t* ci, const double* v, int np, const int32_t* bnd,
+                      double* wgt) {
+  int st = orc_weights(n, rp, ci, v, wgt);
+  if (st != ORC_OK || np <= 1) return st;
+  for (int i = 0; i < n; ++i) {
+    int pi = part_of(i, np, bnd);
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p)
+      if (part_of(ci[p], np, bnd) != pi) wgt[p] = 0.0;
+  }
   return ORC_OK;
 }
 
@@ -362,12 +384,18 @@ orc_hier* orc_setup(int n, const int32_t* rp, const int32_t* ci, const double* v
   for (int i = 0; i < n; ++i) comp[i] = i;
   int comp_n = n;
   int group = 0;
+  /* row blocks of the decoupled aggregation; block boundaries move to the
+   * aggregate ids of the blocks' first rows after every pairwise step */
+  int np = p->num_parts > 1 ? p->num_parts : 1;
+  if (np > n) np = n;
+  int32_t* bnd = (int32_t*)xcalloc((size_t)np + 1, sizeof(int32_t));
+  for (int q = 0; q <= np; ++q) bnd[q] = (int32_t)(((int64_t)q * n) / np);
 
   while (cur.n > cs && h->nl < p->max_levels && h->nl < ORC_MAXL - 1 && h->npair < ORC_MAXPAIR) {
     double* wgt = (double*)xcalloc((size_t)cur.nnz, sizeof(double));
     int32_t* mate = (int32_t*)xcalloc((size_t)cur.n, sizeof(int32_t));
     int32_t* agg = (int32_t*)xcalloc((size_t)cur.n, sizeof(int32_t));
-    orc_weights(cur.n, cur.rp, cur.ci, cur.v, wgt);
+    orc_weights_parts(cur.n, cur.rp, cur.ci, cur.v, np, bnd, wgt);
     orc_match_greedy(cur.n, cur.rp, cur.ci, wgt, mate);
     int nc = orc_aggregate(cur.n, mate, agg);
     free(wgt);
@@ -385,6 +413,8 @@ orc_hier* orc_setup(int n, const int32_t* rp, const int32_t* ci, const double* v
     nxt.v = (double*)xcalloc((size_t)nnz_c, sizeof(double));
     orc_galerkin(cur.n, cur.rp, cur.ci, cur.v, agg, nc, nxt.rp, nxt.ci, nxt.v);
     for (int i = 0; i < comp_n; ++i) comp[i] = agg[comp[i]];
+    for (int q = 0; q < np; ++q) bnd[q] = bnd[q] < cur.n ? agg[bnd[q]] : nc;
+    bnd[np] = nc;
     free(agg);
     csr_free(&cur);
     cur = nxt;
@@ -410,6 +440,7 @@ orc_hier* orc_setup(int n, const int32_t* rp, const int32_t* ci, const double* v
     free(comp);
   }
   csr_free(&cur);
+  free(bnd);
 
   for (int k = 0; k < h->nl; ++k) {
     int nk = h->A[k].n;
@@ -534,6 +565,17 @@ static void vcycle_d(orc_hier* h, int k, const double* r, double* z) {
   }
   for (int i = 0; i < n; ++i) rc[agg[i]] += tmp[i];
   vcycle_d(h, k + 1, rc, zc);
+  if (h->p.cycle == 2) {
+    /* W-cycle: a second coarse correction on the updated coarse residual */
+    double* rc2 = (double*)xcalloc((size_t)nc, sizeof(double));
+    double* ec2 = (double*)xcalloc((size_t)nc, sizeof(double));
+    orc_spmv(h, k + 1, zc, rc2);
+    for (int J = 0; J < nc; ++J) rc2[J] = rc[J] - rc2[J];
+    vcycle_d(h, k + 1, rc2, ec2);
+    for (int J = 0; J < nc; ++J) zc[J] += ec2[J];
+    free(rc2);
+    free(ec2);
+  }
   for (int i = 0; i < n; ++i) z[i] += zc[agg[i]]; /* prolongation, unit P */
   for (int s = 0; s < h->p.post_sweeps; ++s) sweep_d(A, h->dinv[k], r, z, tmp);
   free(rc);
@@ -591,6 +633,28 @@ static void vcycle_f(orc_hier* h, int k, const float* r, float* z) {
   }
   for (int i = 0; i < n; ++i) rc[agg[i]] += tmp[i];
   vcycle_f(h, k + 1, rc, zc);
+  if (h->p.cycle == 2) {
+    float* rc2 = (float*)xcalloc((size_t)nc, sizeof(float));
+    float* ec2 = (float*)xcalloc((size_t)nc, sizeof(float));
+    const ocsr* C = &h->A[k + 1];
+    if (k + 1 == h->nl - 1) { /* the coarsest level: FP64 values, float vectors */
+      for (int J = 0; J < nc; ++J) {
+        double s = 0.0;
+        for (int32_t q = C->rp[J]; q < C->rp[J + 1]; ++q) s += C->v[q] * (double)zc[C->ci[q]];
+        rc2[J] = (float)((double)rc[J] - s);
+      }
+    } else {
+      for (int J = 0; J < nc; ++J) {
+        float s = 0.0f;
+        for (int32_t q = C->rp[J]; q < C->rp[J + 1]; ++q) s += h->fval[k + 1][q] * zc[C->ci[q]];
+        rc2[J] = rc[J] - s;
+      }
+    }
+    vcycle_f(h, k + 1, rc2, ec2);
+    for (int J = 0; J < nc; ++J) zc[J] += ec2[J];
+    free(rc2);
+    free(ec2);
+  }
   for (int i = 0; i < n; ++i) z[i] += zc[agg[i]];
   for (int s = 0; s < h->p.post_sweeps; ++s) sweep_f(A, val, D, r, z, tmp);
   free(rc);

@@ -34,6 +34,8 @@ typedef struct orc_params {
   int coarse_solver;   /* ORC_COARSE_L1JACOBI or ORC_COARSE_DENSE_CHOL (exact, pins only) */
   int precision;       /* ORC_FP64 / ORC_FP32 / ORC_FP32_BF16FINE hierarchy emulation */
   int true_res_every;  /* mixed precision: replace r by b - A u every k iterations (50) */
+  int num_parts;       /* decoupled aggregation (Sec. 4.1): matching inside np row blocks (1) */
+  int cycle;           /* Listing 1 cycle_type: 0 V-cycle, 2 W-cycle (0) */
 } orc_params;
 
 typedef struct orc_hier orc_hier;
@@ -42,6 +44,9 @@ void orc_params_default(orc_params* p);
 
 /* single steps (exposed for pins) */
 int orc_weights(int n, const int32_t* rp, const int32_t* ci, const double* v, double* wgt);
+/* weights restricted to the row blocks [bnd[p], bnd[p+1]) (edges across blocks get 0) */
+int orc_weights_parts(int n, const int32_t* rp, const int32_t* ci, const double* v, int np, const int32_t* bnd,
+                      double* wgt);
 int orc_match_greedy(int n, const int32_t* rp, const int32_t* ci, const double* wgt, int32_t* mate);
 int orc_aggregate(int n, const int32_t* mate, int32_t* agg);
 /* Galerkin: first call with out arrays NULL returns nnz_c; second fills them */

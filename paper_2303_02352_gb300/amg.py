@@ -36,7 +36,7 @@ class amg_csr(ctypes.Structure):
 
 
 PARAM_FIELDS = ("aggr_steps", "max_levels", "coarse_size", "pre_sweeps", "post_sweeps", "coarse_sweeps",
-                "precision", "true_res_every", "use_graph", "graph_batch")
+                "precision", "true_res_every", "use_graph", "graph_batch", "num_parts", "cycle")
 
 
 class amg_params(ctypes.Structure):
@@ -48,7 +48,8 @@ class amg_info_t(ctypes.Structure):
                 ("opc", ctypes.c_double), ("num_pairwise", ctypes.c_int32), ("setup_ms", ctypes.c_double),
                 ("vcycle_bytes", ctypes.c_double), ("iteration_bytes", ctypes.c_double),
                 ("vcycle_launches", ctypes.c_int32), ("iteration_launches", ctypes.c_int32),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("setup_match_ms", ctypes.c_double),
+                ("setup_galerkin_ms", ctypes.c_double)]
 
 
 _LIB = None
@@ -177,7 +178,8 @@ class Hierarchy:
         return {"num_levels": L, "n": list(inf.n[:L]), "nnz": list(inf.nnz[:L]), "opc": inf.opc,
                 "num_pairwise": inf.num_pairwise, "setup_ms": inf.setup_ms, "vcycle_bytes": inf.vcycle_bytes,
                 "iteration_bytes": inf.iteration_bytes, "vcycle_launches": inf.vcycle_launches,
-                "iteration_launches": inf.iteration_launches, "precision": inf.precision}
+                "iteration_launches": inf.iteration_launches, "precision": inf.precision,
+                "setup_match_ms": inf.setup_match_ms, "setup_galerkin_ms": inf.setup_galerkin_ms}
 
     @property
     def num_levels(self) -> int:

@@ -77,6 +77,8 @@ struct Level {
   void* zb = nullptr;
   void* t = nullptr;         // residual
   float* r0f = nullptr;      // level 0 low precision: float copy of the FCG residual
+  void* e = nullptr;         // W-cycle: first coarse correction of this level (levels > 0)
+  void* r2 = nullptr;        // W-cycle: input of the second visit (levels > 0)
 };
 
 struct AdjState;  // adjoint work buffers (learned.cu)
@@ -89,6 +91,8 @@ struct amg_handle {
   Level L[AMG_MAXL];
   int npair = 0;
   double setup_ms = 0.0;
+  double match_ms = 0.0;      // setup time in the matching steps
+  double galerkin_ms = 0.0;   // setup time in the Galerkin products
   // FCG vectors
   double *b = nullptr, *u = nullptr, *r = nullptr, *w = nullptr, *d = nullptr, *v = nullptr,
          *q = nullptr;

@@ -22,6 +22,8 @@ extern "C" void amg_params_default(amg_params* p) {
   p->true_res_every = 50;
   p->use_graph = 1;
   p->graph_batch = 4;
+  p->num_parts = 1;
+  p->cycle = 0;
 }
 
 extern "C" amg_status amg_info(const amg_handle* h, amg_info_t* info) {
@@ -42,6 +44,8 @@ extern "C" amg_status amg_info(const amg_handle* h, amg_info_t* info) {
   info->vcycle_launches = h->launches_vcycle;
   info->iteration_launches = h->launches_iter;
   info->precision = h->p.precision;
+  info->setup_match_ms = h->match_ms;
+  info->setup_galerkin_ms = h->galerkin_ms;
   return AMG_OK;
 }
 

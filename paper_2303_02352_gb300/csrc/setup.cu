@@ -16,6 +16,8 @@
 #include <cstring>
 #include <chrono>
 #include <cstdlib>
+#include <algorithm>
+#include <vector>
 
 #include "amg_internal.cuh"
 
@@ -133,16 +135,30 @@ __global__ void k_diag(int n, const int32_t* __restrict__ rp, const int32_t* __r
   dg[i] = d;
 }
 
+// decoupled aggregation (Sec. 4.1): the row block of row i among the np
+// contiguous blocks [bnd[q], bnd[q+1])
+__device__ __forceinline__ int part_of(int i, int np, const int32_t* __restrict__ bnd) {
+  int lo = 0, hi = np - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (i >= bnd[mid]) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 __global__ void k_weights(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                          const double* __restrict__ v, const double* __restrict__ dg, double* __restrict__ wgt) {
+                          const double* __restrict__ v, const double* __restrict__ dg, int np,
+                          const int32_t* __restrict__ bnd, double* __restrict__ wgt) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double wi = 1.0, wj = 1.0;
   const double di = dg[i];
+  const int pi = np > 1 ? part_of(i, np, bnd) : 0;
   for (int p = rp[i]; p < rp[i + 1]; ++p) {
     int j = ci[p];
     double a = v[p];
-    if (j == i || a == 0.0) {
+    if (j == i || a == 0.0 || (np > 1 && part_of(j, np, bnd) != pi)) {
       wgt[p] = 0.0;
       continue;
     }
@@ -418,6 +434,12 @@ __global__ void k_mirror(int nc, const int32_t* __restrict__ rp, const int32_t* 
   }
 }
 
+// block boundaries move to the aggregate ids of the blocks' first rows
+__global__ void k_update_bnd(int np, int32_t* bnd, const int32_t* __restrict__ agg, int nfine, int nc) {
+  for (int q = threadIdx.x; q < np; q += blockDim.x) bnd[q] = bnd[q] < nfine ? agg[bnd[q]] : nc;
+  if (threadIdx.x == 0) bnd[np] = nc;
+}
+
 __global__ void k_compose(int n, int32_t* __restrict__ comp, const int32_t* __restrict__ agg) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) comp[i] = agg[comp[i]];
@@ -520,8 +542,8 @@ static amg_status check_flags(amg_handle* h, const char* where) {
 }
 
 // one pairwise step: matching on `cur`, aggregation; returns nc and agg (device)
-static amg_status pairwise_step(amg_handle* h, const PCsr& cur, int32_t* agg, int32_t* open_idx, int32_t* mate,
-                                int* nc_out) {
+static amg_status pairwise_step(amg_handle* h, const PCsr& cur, int np, const int32_t* bnd, int32_t* agg,
+                                int32_t* open_idx, int32_t* mate, int* nc_out) {
   cudaStream_t s = h->stream;
   const int n = cur.n;
   const int64_t nnz = cur.nnz;
@@ -543,7 +565,7 @@ static amg_status pairwise_step(amg_handle* h, const PCsr& cur, int32_t* agg, in
   AMG_ALLOC(h, suitor, unsigned long long, n);
   const int nb = amg_blocks(n);
   k_diag<<<nb, AMG_BLOCK, 0, s>>>(n, cur.rp, cur.ci, cur.v, dg);
-  k_weights<<<nb, AMG_BLOCK, 0, s>>>(n, cur.rp, cur.ci, cur.v, dg, wgt);
+  k_weights<<<nb, AMG_BLOCK, 0, s>>>(n, cur.rp, cur.ci, cur.v, dg, np, bnd, wgt);
   k_rank<<<nb, AMG_BLOCK, 0, s>>>(n, cur.rp, cur.ci, wgt, rank_of, srt_pos, cnt);
   k_other_rank<<<nb, AMG_BLOCK, 0, s>>>(n, cur.rp, cur.ci, rank_of, srt_pos, cnt, srt_col, key_rank, h->dev_flags);
   AMG_CK(h, cudaMemsetAsync(suitor, 0xff, sizeof(unsigned long long) * (size_t)n, s));
@@ -671,14 +693,26 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
   AMG_ALLOC(h, comp, int32_t, n);
   k_iota<<<amg_blocks(n), AMG_BLOCK, 0, s>>>(n, comp);
   int comp_n = n, group = 0;
+  // row blocks of the decoupled aggregation
+  const int np = std::max(1, std::min(h->p.num_parts, n));
+  int32_t* bnd;
+  {
+    std::vector<int32_t> hb(np + 1);
+    for (int q = 0; q <= np; ++q) hb[q] = (int32_t)(((int64_t)q * n) / np);
+    AMG_ALLOC(h, bnd, int32_t, np + 1);
+    AMG_CK(h, cudaMemcpy(bnd, hb.data(), sizeof(int32_t) * (np + 1), cudaMemcpyHostToDevice));
+  }
   while (cur.n > cs && h->nl < maxl) {
     int32_t *agg, *open_idx, *mate;
     AMG_ALLOC(h, agg, int32_t, cur.n);
     AMG_ALLOC(h, open_idx, int32_t, cur.n);
     AMG_ALLOC(h, mate, int32_t, cur.n);
     int nc = 0;
-    amg_status st = pairwise_step(h, cur, agg, open_idx, mate, &nc);
+    auto tm0 = std::chrono::steady_clock::now();
+    amg_status st = pairwise_step(h, cur, np, bnd, agg, open_idx, mate, &nc);
     if (st != AMG_OK) return st;
+    auto tm1 = std::chrono::steady_clock::now();
+    h->match_ms += std::chrono::duration<double, std::milli>(tm1 - tm0).count();
     if (nc == cur.n) {  // no edge matched
       amg_release(h, agg);
       amg_release(h, open_idx);
@@ -688,7 +722,10 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
     PCsr nxt;
     st = galerkin_step(h, cur, agg, open_idx, mate, nc, &nxt);
     if (st != AMG_OK) return st;
+    AMG_CK(h, cudaStreamSynchronize(s));
+    h->galerkin_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tm1).count();
     k_compose<<<amg_blocks(comp_n), AMG_BLOCK, 0, s>>>(comp_n, comp, agg);
+    if (np > 1) k_update_bnd<<<1, 256, 0, s>>>(np, bnd, agg, cur.n, nc);
     amg_release(h, agg);
     amg_release(h, open_idx);
     amg_release(h, mate);
@@ -769,7 +806,9 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
   }
   // fused bottom: the levels k >= 1 with at most 16384 rows (at most 8 of them)
   h->kb = h->nl;
-  if (h->use_bottom)
+  if (h->p.cycle != 0 && h->p.cycle != 2)
+    return amg_fail(h, AMG_ERR_INVALID_ARG, "cycle must be 0 (V) or 2 (W)");
+  if (h->use_bottom && h->p.cycle == 0)
     for (int k = 1; k < h->nl; ++k)
       if (h->L[k].n <= 16384 && h->nl - k <= 8) {
         h->kb = k;

@@ -155,6 +155,13 @@ __global__ void k_copy(int n, const VT* __restrict__ a, OT* __restrict__ b, cons
 }
 
 template <typename VT>
+__global__ void k_add(int n, const VT* __restrict__ x, VT* __restrict__ y, const int* skip) {
+  if (*skip) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += x[i];
+}
+
+template <typename VT>
 __global__ void k_zero(int n, VT* __restrict__ a, const int* skip) {
   if (*skip) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -548,10 +555,23 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
     R.add(4.0 * n + sc * nc + 2.0 * sx * n);
     return;
   }
+  const bool wcyc = h->p.cycle == 2;
   if (k + 1 == h->nl - 1) {  // coarsest: FP64
     k_restrict<VT, double><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, L.mptr, L.mem, t, (double*)C.r, R.skip);
     R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 8.0 * nc);
     double* zc = rec_coarse(R, k + 1, (const double*)C.r, nullptr);
+    if (wcyc) {  // W-cycle: e = z_c;  r2 = r_c - A_c e;  e += B_c r2
+      double* e = (double*)C.e;
+      double* r2 = (double*)C.r2;
+      k_copy<double, double><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, zc, e, R.skip);
+      launch_resid<double, double>(R.s, C, C.v, (const double*)C.r, e, r2, R.skip, h->dev_flags, h->stages);
+      double* zc2 = rec_coarse(R, k + 1, r2, nullptr);
+      k_add<double><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, zc2, e, R.skip);
+      R.add(16.0 * nc);
+      R.add(row_pass(C, 8.0) + 24.0 * nc);
+      R.add(24.0 * nc);
+      zc = e;
+    }
     k_prolong<VT, double><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, L.agg, zc, z, R.skip);
     R.add(4.0 * n + 8.0 * nc + 2.0 * sx * n);
   } else {
@@ -561,6 +581,23 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
     VT* zc;
     if (C.lowp) zc = (VT*)rec_level<float, float, float>(R, k + 1, (const float*)C.r, nullptr);
     else zc = (VT*)rec_level<double, double, double>(R, k + 1, (const double*)C.r, nullptr);
+    if (wcyc) {
+      VT* e = (VT*)C.e;
+      VT* r2 = (VT*)C.r2;
+      k_copy<VT, VT><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, zc, e, R.skip);
+      if (C.lowp) launch_resid<float, float>(R.s, C, C.vf, (const float*)C.r, (const float*)e, (float*)r2, R.skip,
+                                             h->dev_flags, h->stages);
+      else launch_resid<double, double>(R.s, C, C.v, (const double*)C.r, (const double*)e, (double*)r2, R.skip,
+                                        h->dev_flags, h->stages);
+      VT* zc2;
+      if (C.lowp) zc2 = (VT*)rec_level<float, float, float>(R, k + 1, (const float*)r2, nullptr);
+      else zc2 = (VT*)rec_level<double, double, double>(R, k + 1, (const double*)r2, nullptr);
+      k_add<VT><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, zc2, e, R.skip);
+      R.add(2.0 * sc * nc);
+      R.add(row_pass(C, val_bytes(C)) + 3.0 * sc * nc);
+      R.add(3.0 * sc * nc);
+      zc = e;
+    }
     k_prolong<VT, VT><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, L.agg, zc, z, R.skip);
     R.add(4.0 * n + sc * nc + 2.0 * sx * n);
   }
@@ -708,6 +745,9 @@ amg_status amg_prepare_solve(amg_handle* h) {
     if (!(L.za = amg_alloc(h, es * L.n)) || !(L.zb = amg_alloc(h, es * L.n)) || !(L.t = amg_alloc(h, es * L.n)))
       return amg_fail(h, AMG_ERR_OOM, "work vectors of level %d", k);
     if (k > 0 && !(L.r = amg_alloc(h, es * L.n))) return amg_fail(h, AMG_ERR_OOM, "level input %d", k);
+    if (k > 0 && h->p.cycle == 2 &&
+        (!(L.e = amg_alloc(h, es * L.n)) || !(L.r2 = amg_alloc(h, es * L.n))))
+      return amg_fail(h, AMG_ERR_OOM, "W-cycle vectors of level %d", k);
     if (k == 0 && L.lowp) AMG_ALLOC(h, L.r0f, float, L.n);
   }
   AMG_ALLOC(h, h->b, double, n);

@@ -307,3 +307,32 @@ def test_fused_bottom_matches_separate_launches(name, prec, monkeypatch):
     monkeypatch.setenv("AMG_SMALL_ROWS", "100000000")
     z2 = G(A, precision=prec).vcycle(r).cpu().numpy()
     assert rel(z2, z0) < (1e-13 if prec == 0 else 1e-6)
+
+
+@pytest.mark.parametrize("np_", [2, 5])
+def test_decoupled_aggregation_parity(np_):
+    A = W.diffusion27(12, 2.0, 21)
+    g, o = G(A, num_parts=np_), O.Hierarchy(A, num_parts=np_)
+    assert g.num_levels == o.num_levels
+    for k in range(o.num_levels - 1):
+        assert np.array_equal(g.aggregates(k), o.level_agg(k))
+    for k in range(o.num_levels):
+        assert np.array_equal(g.level_csr(k)[2].view(np.uint64), o.level_csr(k)[2].view(np.uint64))
+    r = W.random_vector(A.n, 3)
+    assert rel(g.vcycle(r).cpu().numpy(), o.vcycle(r)) < 1e-12
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 4))
+    assert abs(g.pcg_solve(b)["iters"] - o.fcg(b)["iters"]) <= 1
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_wcycle_parity(prec):
+    A = W.poisson7(20)
+    g, o = G(A, cycle=2, precision=prec), O.Hierarchy(A, cycle=2, precision=prec)
+    r = W.random_vector(A.n, 5)
+    assert rel(g.vcycle(r).cpu().numpy(), o.vcycle(r)) < (1e-12 if prec == 0 else 1e-4)
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 6))
+    rg, ro = g.pcg_solve(b), o.fcg(b)
+    assert abs(rg["iters"] - ro["iters"]) <= (1 if prec == 0 else 2) and rg["true_rel_res"] < 1e-6
+    assert rg["iters"] <= G(A, precision=prec).pcg_solve(b)["iters"]
+    info = g.info()
+    assert info["setup_match_ms"] > 0 and info["setup_galerkin_ms"] > 0

@@ -509,3 +509,58 @@ def test_features_reference_on_poisson():
     assert np.allclose(f[i], [0.5, 0.0, 7 / 27, 0.0])
     # corner row: 4 entries, l1 = 9 ; neighbours have l1 = 10
     assert np.allclose(f[0], [6 / 9, np.log(9) - np.mean(np.log([9, 10, 10, 10])), 4 / 27, 0.0])
+
+
+# ----------------------------------------------------------------------------
+# decoupled aggregation (Sec. 4.1) and the W-cycle (Listing 1 cycle_type 2)
+
+
+def test_decoupled_matching_1d_closed_form():
+    A = W.laplace1d(10)
+    h = O.Hierarchy(A, num_parts=2, coarse_size=8, aggr_steps=1)
+    # blocks [0,5) and [5,10): (0,1),(2,3), 4 alone | (5,6),(7,8), 9 alone
+    agg = h.level_agg(0)
+    assert list(agg) == [0, 0, 1, 1, 2, 3, 3, 4, 4, 5]
+
+
+@pytest.mark.parametrize("np_", [1, 3, 8])
+def test_decoupled_aggregates_stay_inside_blocks(np_):
+    A = W.diffusion7(14, 1.5, 17)
+    h = O.Hierarchy(A, num_parts=np_)
+    href = O.Hierarchy(A)
+    if np_ == 1:
+        for k in range(h.num_levels - 1):
+            assert np.array_equal(h.level_agg(k), href.level_agg(k))
+    # composed map of level 0: every aggregate lies in one block of level 0
+    agg = h.level_agg(0)
+    bnd = [(q * A.n) // np_ for q in range(np_ + 1)]
+    part = np.searchsorted(bnd, np.arange(A.n), side="right") - 1
+    for J in range(h.level_n(1)):
+        assert len(set(part[agg == J])) == 1
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 2))
+    assert h.fcg(b)["status"] == O.OK
+
+
+def test_wcycle_equals_error_propagation_formula():
+    A = W.diffusion7(5, 1.0, 13)
+    h = O.Hierarchy(A, coarse_size=8, aggr_steps=2, cycle=2)
+    assert h.num_levels >= 3
+    B = dense_B(h, A.n)
+
+    def ew(k):
+        rp, ci, v = h.level_csr(k)
+        n = h.level_n(k)
+        Ak = dense(rp, ci, v, n)
+        S = np.eye(n) - np.diag(1.0 / np.abs(Ak).sum(axis=1)) @ Ak
+        if k == h.num_levels - 1:
+            return np.linalg.matrix_power(S, 20)
+        P = prolongator(h.level_agg(k), h.level_n(k + 1)).toarray()
+        rpc, cic, vc = h.level_csr(k + 1)
+        Ac = dense(rpc, cic, vc, h.level_n(k + 1))
+        Ec = ew(k + 1)
+        Bc = (np.eye(len(Ac)) - Ec @ Ec) @ np.linalg.inv(Ac)  # two coarse visits
+        return np.linalg.matrix_power(S, 4) @ (np.eye(n) - P @ Bc @ P.T @ Ak) @ np.linalg.matrix_power(S, 4)
+
+    Ad = A.to_scipy().toarray()
+    assert np.allclose(np.eye(A.n) - B @ Ad, ew(0), atol=1e-12)
+    assert np.allclose(B, B.T, atol=1e-13)
