@@ -110,6 +110,7 @@ struct amg_handle {
   int use_pipe = 1;            // 0: non-pipelined tiled row kernels
   int use_bottom = 0;          // 1: bottom levels in one cluster launch (measured slower; off)
   int small_rows = 0;          // levels with fewer rows use the non-pipelined tiled kernels
+  int min_tpr = 1;             // tuning hook: least threads per row of the pipelined kernels
   int kb = AMG_MAXL;           // first level of the fused bottom (nl: none)
   long long suitor_cap = -1;   // test hook: step cap of the matching loop (-1: proof-level bound)
   int fail_alloc_after = -1;   // test hook: the allocation with this index fails (-1: never)
@@ -155,12 +156,12 @@ __host__ __device__ constexpr int amg_pipe_tile_bytes(int value_bytes) {
   return value_bytes >= 8 ? 24576 : (value_bytes >= 4 ? 16384 : 12288);
 }
 
-// tile height of the row kernels: the largest of 256, 128, 64, 32 rows whose
-// longest-row bound fits one pipeline stage
-static inline int amg_tile_rows(int maxrow, int value_bytes) {
+// tile height of the row kernels: the largest power of two R <= 256 rows
+// (at least rmin) whose longest-row bound fits one pipeline stage
+static inline int amg_tile_rows(int maxrow, int value_bytes, int rmin = 32) {
   const int cap = amg_pipe_tile_bytes(value_bytes) / (value_bytes + 4);
   int R = 256;
-  while (R > 32 && (int64_t)R * maxrow > cap) R /= 2;
+  while (R > rmin && (int64_t)R * maxrow > cap) R /= 2;
   return R;
 }
 

@@ -121,13 +121,18 @@ __device__ __forceinline__ bool mbar_wait_warp(unsigned long long* bar, uint32_t
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
 
-// Warp-specialised persistent row kernel: R/32 consumer warps (one row per
-// thread) and one producer warp.  Per stage a "full" barrier (the producer's
+#define PIPE_CONSUMERS 256
+
+// Warp-specialised persistent row kernel: 8 consumer warps and one producer
+// warp.  A tile holds R = 256 / TPR rows; TPR threads share a row (entries
+// strided by TPR, summed with shuffles), so that long rows still keep 256
+// threads busy per tile; TPR = 1 for short rows (one thread per row).  Per stage a "full" barrier (the producer's
 // expect_tx plus the bytes of the two bulk copies) and an "empty" barrier (one
 // arrival per consumer warp once it has read the stage).  No block-wide
 // barrier inside the tile loop: warps drift up to S tiles apart.
-template <int R, int S, int MODE, typename MT, typename VT, typename OT>
-__global__ void __launch_bounds__(R + 32) k_rows_pipe(const RowArgs<MT, VT, OT> a) {
+template <int TPR, int S, int MODE, typename MT, typename VT, typename OT>
+__global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs<MT, VT, OT> a) {
+  constexpr int R = PIPE_CONSUMERS / TPR;
   if constexpr (MODE == PM_SWEEP || MODE == PM_RESID) {
     if (*a.skip) return;
   } else if constexpr (MODE == PM_DOTS) {
@@ -139,7 +144,7 @@ __global__ void __launch_bounds__(R + 32) k_rows_pipe(const RowArgs<MT, VT, OT> 
   auto* P = reinterpret_cast<PipeSmem<MT, S>*>(smem_raw);
   __shared__ double red[96];
   constexpr int VE = PipeTile<MT>::VE;
-  constexpr int NCW = R / 32;  // consumer warps
+  constexpr int NCW = PIPE_CONSUMERS / 32;  // consumer warps
   const int n = a.n;
   const int ntiles = (n + R - 1) / R;
   const int G = gridDim.x;
@@ -195,14 +200,18 @@ __global__ void __launch_bounds__(R + 32) k_rows_pipe(const RowArgs<MT, VT, OT> 
       if (tile >= ntiles) break;
       const int stage = k % S;
       const int row0 = tile * R, row1 = min(row0 + R, n);
-      const int row = row0 + (int)threadIdx.x;
+      const int sub = (int)threadIdx.x % TPR;  // lane within the row's group
+      const int row = row0 + (int)threadIdx.x / TPR;
       const bool live = row < row1;
+      const bool lead = live && sub == 0;      // the lane that finishes the row
       const int p0 = __ldg(&a.rp[row0]);
       int q0 = 0, q1 = 0;
       VT own = 0, rr = 0, dd = 0, qq = 0;
       if (live) {
-        q0 = __ldg(&a.rp[row]);
+        q0 = __ldg(&a.rp[row]) + sub;
         q1 = __ldg(&a.rp[row + 1]);
+      }
+      if (lead) {
         if constexpr (MODE == PM_SWEEP) {
           own = __ldg(&a.x[row]);
           rr = __ldg(&a.r[row]);
@@ -225,10 +234,11 @@ __global__ void __launch_bounds__(R + 32) k_rows_pipe(const RowArgs<MT, VT, OT> 
       const PipeTile<MT>& T = P->st[stage];
       VT s = 0;
 #pragma unroll 8
-      for (int q = q0; q < q1; ++q) s += (VT)to_acc(T.v[q - av]) * __ldg(&a.x[T.c[q - ac]]);
+      for (int q = q0; q < q1; q += TPR) s += (VT)to_acc(T.v[q - av]) * __ldg(&a.x[T.c[q - ac]]);
+      if constexpr (TPR > 1) s = group_sum<TPR>(s);
       __syncwarp();
       if (lane == 0) mbar_arrive(&P->empty[stage]);  // this warp is done with the stage
-      if (live) {
+      if (lead) {
         if constexpr (MODE == PM_SWEEP) {
           a.out[row] = (OT)(own + dd * (rr - s));
         } else if constexpr (MODE == PM_RESID) {
@@ -280,16 +290,17 @@ __global__ void __launch_bounds__(R + 32) k_rows_pipe(const RowArgs<MT, VT, OT> 
 
 // grid of a persistent pipelined kernel: one wave of resident blocks, at most
 // one block per tile
-template <int R, int S, int MODE, typename MT, typename VT, typename OT>
+template <int TPR, int S, int MODE, typename MT, typename VT, typename OT>
 static int pipe_grid(int n) {
   static int bps = -1;
   constexpr int smem = (int)sizeof(PipeSmem<MT, S>);
-  auto kern = k_rows_pipe<R, S, MODE, MT, VT, OT>;
+  constexpr int R = PIPE_CONSUMERS / TPR;
+  auto kern = k_rows_pipe<TPR, S, MODE, MT, VT, OT>;
   if (bps < 0) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, R + 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, PIPE_CONSUMERS + 32, smem);
     bps = b < 1 ? 1 : b;
   }
   const int ntiles = (n + R - 1) / R;
@@ -297,9 +308,9 @@ static int pipe_grid(int n) {
   return ntiles < g ? ntiles : g;
 }
 
-template <int R, int S, int MODE, typename MT, typename VT, typename OT>
+template <int TPR, int S, int MODE, typename MT, typename VT, typename OT>
 static void launch_pipe(cudaStream_t s, const RowArgs<MT, VT, OT>& a) {
-  const int grid = pipe_grid<R, S, MODE, MT, VT, OT>(a.n);
+  const int grid = pipe_grid<TPR, S, MODE, MT, VT, OT>(a.n);
   constexpr int smem = (int)sizeof(PipeSmem<MT, S>);
-  k_rows_pipe<R, S, MODE, MT, VT, OT><<<grid, R + 32, smem, s>>>(a);
+  k_rows_pipe<TPR, S, MODE, MT, VT, OT><<<grid, PIPE_CONSUMERS + 32, smem, s>>>(a);
 }

@@ -785,8 +785,13 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
     L.Rd = amg_tile_rows(mr, 8);
     L.R = amg_tile_rows(mr, vb);
     const bool big = L.n >= h->small_rows;
-    L.piped = h->use_pipe && (int64_t)L.Rd * mr <= amg_pipe_tile_bytes(8) / 12;
-    L.pipe = h->use_pipe && big && (int64_t)L.R * mr <= amg_pipe_tile_bytes(vb) / (vb + 4);
+    // pipelined kernels: tile heights down to 8 rows (32 threads per row)
+    const int Rp = std::min(amg_tile_rows(mr, vb, 8), 256 / std::max(1, h->min_tpr));
+    const int Rpd = std::min(amg_tile_rows(mr, 8, 8), 256 / std::max(1, h->min_tpr));
+    L.piped = h->use_pipe && (int64_t)Rpd * mr <= amg_pipe_tile_bytes(8) / 12;
+    L.pipe = h->use_pipe && big && (int64_t)Rp * mr <= amg_pipe_tile_bytes(vb) / (vb + 4);
+    if (L.piped) L.Rd = Rpd;
+    if (L.pipe) L.R = Rp;
     AMG_ALLOC(h, L.l1, double, L.n);
     AMG_ALLOC(h, L.dinv, double, L.n);
     if (L.lowp) {
@@ -836,6 +841,7 @@ extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* str
   if (const char* e = getenv("AMG_SUITOR_CAP")) h->suitor_cap = atoll(e);
   if (const char* e = getenv("AMG_BOTTOM")) h->use_bottom = atoi(e);
   if (const char* e = getenv("AMG_SMALL_ROWS")) h->small_rows = atoi(e);
+  if (const char* e = getenv("AMG_MIN_TPR")) h->min_tpr = atoi(e);
   if (const char* e = getenv("AMG_FAIL_ALLOC_AFTER")) h->fail_alloc_after = atoi(e);
   if (const char* e = getenv("AMG_PIPE")) h->use_pipe = atoi(e);
   if (const char* e = getenv("AMG_STAGES")) h->stages = atoi(e);

@@ -368,14 +368,20 @@ int amg_num_sms() {
     default: { constexpr int TR = 32; CALL; } break;   \
   }
 
-#define DISPATCH_S(SS, CALL)                          \
-  if ((SS) == 2) { constexpr int TS = 2; CALL; }      \
-  else if ((SS) == 4) { constexpr int TS = 4; CALL; } \
-  else { constexpr int TS = 3; CALL; }
+// pipelined kernels: two stages (measured best); dispatch on threads per row
+#define DISPATCH_TPR(TT, CALL)                          \
+  switch (TT) {                                         \
+    case 1: { constexpr int TP = 1; CALL; } break;      \
+    case 2: { constexpr int TP = 2; CALL; } break;      \
+    case 4: { constexpr int TP = 4; CALL; } break;      \
+    case 8: { constexpr int TP = 8; CALL; } break;      \
+    case 16: { constexpr int TP = 16; CALL; } break;    \
+    default: { constexpr int TP = 32; CALL; } break;    \
+  }
 
 template <int MODE, typename MT, typename VT, typename OT>
-static void launch_rows(cudaStream_t s, int R, int S, const RowArgs<MT, VT, OT>& a) {
-  DISPATCH_R(R, DISPATCH_S(S, (launch_pipe<TR, TS, MODE, MT, VT, OT>(s, a))));
+static void launch_rows(cudaStream_t s, int R, int /*stages*/, const RowArgs<MT, VT, OT>& a) {
+  DISPATCH_TPR(PIPE_CONSUMERS / R, (launch_pipe<TP, 2, MODE, MT, VT, OT>(s, a)));
 }
 
 template <typename MT, typename VT, typename OT>

@@ -307,6 +307,15 @@ def test_fused_bottom_matches_separate_launches(name, prec, monkeypatch):
     monkeypatch.setenv("AMG_SMALL_ROWS", "100000000")
     z2 = G(A, precision=prec).vcycle(r).cpu().numpy()
     assert rel(z2, z0) < (1e-13 if prec == 0 else 1e-6)
+    # several threads per row in the pipelined kernels
+    monkeypatch.setenv("AMG_SMALL_ROWS", "0")
+    for tpr in ("4", "32"):
+        monkeypatch.setenv("AMG_MIN_TPR", tpr)
+        gg = G(A, precision=prec)
+        z3 = gg.vcycle(r).cpu().numpy()
+        assert rel(z3, z0) < (1e-13 if prec == 0 else 1e-6)
+        b = W.rhs_from_solution(A, W.random_vector(A.n, 3))
+        assert gg.pcg_solve(b)["true_rel_res"] < 1e-6
 
 
 @pytest.mark.parametrize("np_", [2, 5])
