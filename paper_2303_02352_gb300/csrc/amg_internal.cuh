@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -177,6 +178,31 @@ amg_status amg_capture_graphs(amg_handle* h);
 
 // ---------------------------------------------------------------------------
 // device-side helpers
+
+// Programmatic dependent launch: a kernel lets the next kernel in the stream
+// start early (launch_dependents) and, before it touches data written by the
+// previous kernel, waits for that kernel's completion and memory (wait).  Both
+// are no-ops for kernels launched without the programmatic attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// launch with the programmatic-serialization attribute when enabled
+bool amg_pdl_enabled();
+template <typename... KArgs, typename... Args>
+static inline cudaError_t amg_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                     Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = amg_pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 __device__ __forceinline__ double to_acc(double x) { return x; }
 __device__ __forceinline__ float to_acc(float x) { return x; }

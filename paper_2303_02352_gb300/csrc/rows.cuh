@@ -133,13 +133,7 @@ __device__ __forceinline__ bool mbar_wait_warp(unsigned long long* bar, uint32_t
 template <int TPR, int S, int MODE, typename MT, typename VT, typename OT>
 __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs<MT, VT, OT> a) {
   constexpr int R = PIPE_CONSUMERS / TPR;
-  if constexpr (MODE == PM_SWEEP || MODE == PM_RESID) {
-    if (*a.skip) return;
-  } else if constexpr (MODE == PM_DOTS) {
-    if (a.st->done) return;
-  } else if constexpr (MODE == PM_RTRUE) {
-    if (a.st->done || !a.st->need_true) return;
-  }
+  pdl_trigger();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   auto* P = reinterpret_cast<PipeSmem<MT, S>*>(smem_raw);
   __shared__ double red[96];
@@ -159,31 +153,59 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
   }
   __syncthreads();
 
+  // copies of this block's k-th tile (producer lane only); the matrix does not
+  // change during a solve, so the first S tiles are requested before waiting
+  // for the previous kernel
+  auto issue = [&](int k, int stage) {
+    const int tile = blockIdx.x + k * G;
+    const int row0 = tile * R, row1 = min(row0 + R, n);
+    const int p0 = __ldg(&a.rp[row0]), p1 = __ldg(&a.rp[row1]);
+    const int av = p0 & ~(VE - 1), ac = p0 & ~3;
+    const uint32_t bv = (uint32_t)(((p1 - av) * (int)sizeof(MT) + 15) & ~15);
+    const uint32_t bc = (uint32_t)(((p1 - ac) * 4 + 15) & ~15);
+    mbar_expect_tx(&P->full[stage], bv + bc);
+    tma_load_1d(P->st[stage].v, a.v + av, bv, &P->full[stage]);
+    tma_load_1d(P->st[stage].c, a.ci + ac, bc, &P->full[stage]);
+  };
+  const bool producer = warp == NCW && lane == 0;
+  int issued = 0;
+  // the true-residual check usually has nothing to do: read its flags first
+  constexpr bool early = MODE != PM_RTRUE;
+  if (!early) pdl_wait();
+  if (early && producer)
+    for (; issued < S && blockIdx.x + issued * G < ntiles; ++issued) issue(issued, issued);
+
+  if (early) pdl_wait();  // the previous kernel's results (vectors, flags) are visible from here on
+  bool skip = false;
+  if constexpr (MODE == PM_SWEEP || MODE == PM_RESID) skip = *a.skip != 0;
+  else if constexpr (MODE == PM_DOTS) skip = a.st->done != 0;
+  else if constexpr (MODE == PM_RTRUE) skip = a.st->done || !a.st->need_true;
+  if (skip) {
+    if (producer)  // drain the copies already requested, bounded
+      for (int k = 0; k < issued; ++k) mbar_wait(&P->full[k % S], 0);
+    return;
+  }
+  if (!early && producer)
+    for (; issued < S && blockIdx.x + issued * G < ntiles; ++issued) issue(issued, issued);
+
   double acc[3] = {0.0, 0.0, 0.0};
   const bool first = (MODE == PM_DOTS) ? (a.st->it == 0) : false;
 
   if (warp == NCW) {
     // ---------------- producer warp ----------------
     if (lane == 0) {
-      int k = 0;
+      int k = issued;
       bool aborted = false;
       for (;; ++k) {
         const int tile = blockIdx.x + k * G;
         if (tile >= ntiles) break;
         const int stage = k % S;
-        if (k >= S && !mbar_wait(&P->empty[stage], (uint32_t)(((k / S) - 1) & 1))) {
+        if (!mbar_wait(&P->empty[stage], (uint32_t)(((k / S) - 1) & 1))) {
           atomicOr(a.flags, ST_TIMEOUT);
           aborted = true;
           break;
         }
-        const int row0 = tile * R, row1 = min(row0 + R, n);
-        const int p0 = __ldg(&a.rp[row0]), p1 = __ldg(&a.rp[row1]);
-        const int av = p0 & ~(VE - 1), ac = p0 & ~3;
-        const uint32_t bv = (uint32_t)(((p1 - av) * (int)sizeof(MT) + 15) & ~15);
-        const uint32_t bc = (uint32_t)(((p1 - ac) * 4 + 15) & ~15);
-        mbar_expect_tx(&P->full[stage], bv + bc);
-        tma_load_1d(P->st[stage].v, a.v + av, bv, &P->full[stage]);
-        tma_load_1d(P->st[stage].c, a.ci + ac, bc, &P->full[stage]);
+        issue(k, stage);
       }
       if (aborted) {  // drain: the last copy issued into each stage, bounded
         for (int j = 1; j <= S && k - j >= 0; ++j) {
@@ -312,5 +334,5 @@ template <int TPR, int S, int MODE, typename MT, typename VT, typename OT>
 static void launch_pipe(cudaStream_t s, const RowArgs<MT, VT, OT>& a) {
   const int grid = pipe_grid<TPR, S, MODE, MT, VT, OT>(a.n);
   constexpr int smem = (int)sizeof(PipeSmem<MT, S>);
-  k_rows_pipe<TPR, S, MODE, MT, VT, OT><<<grid, PIPE_CONSUMERS + 32, smem, s>>>(a);
+  amg_launch(k_rows_pipe<TPR, S, MODE, MT, VT, OT>, dim3(grid), dim3(PIPE_CONSUMERS + 32), (size_t)smem, s, a);
 }

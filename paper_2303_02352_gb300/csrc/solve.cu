@@ -9,6 +9,7 @@
 // set: the FCG iteration is replayed as a CUDA graph in batches and the
 // iterations after convergence cost one flag read per kernel.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "amg_internal.cuh"
@@ -78,6 +79,8 @@ __device__ __forceinline__ AT tile_row_dot(TileSmem<MT>& sm, int row0, int row1,
 template <typename RT, typename VT>
 __global__ void __launch_bounds__(AMG_BLOCK) k_first(int n, const VT* __restrict__ dinv, const RT* __restrict__ r,
                                                      VT* __restrict__ rcopy, VT* __restrict__ z, const int* skip) {
+  pdl_trigger();
+  pdl_wait();
   if (*skip) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -92,6 +95,8 @@ __global__ void __launch_bounds__(R) k_sweep(int n, const int32_t* __restrict__ 
                                              const MT* __restrict__ v, const VT* __restrict__ dinv,
                                              const VT* __restrict__ r, const VT* __restrict__ z,
                                              OT* __restrict__ zout, const int* skip) {
+  pdl_trigger();
+  pdl_wait();
   if (*skip) return;
   __shared__ __align__(16) TileSmem<MT> sm;
   const int row0 = blockIdx.x * R, row1 = min(row0 + R, n);
@@ -105,6 +110,8 @@ template <int R, typename MT, typename VT>
 __global__ void __launch_bounds__(R) k_resid(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                              const MT* __restrict__ v, const VT* __restrict__ r,
                                              const VT* __restrict__ z, VT* __restrict__ tout, const int* skip) {
+  pdl_trigger();
+  pdl_wait();
   if (*skip) return;
   __shared__ __align__(16) TileSmem<MT> sm;
   const int row0 = blockIdx.x * R, row1 = min(row0 + R, n);
@@ -129,6 +136,8 @@ __global__ void __launch_bounds__(R) k_spmv(int n, const int32_t* __restrict__ r
 template <typename VT, typename CT>
 __global__ void __launch_bounds__(AMG_BLOCK) k_restrict(int nc, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
                                                         const VT* __restrict__ t, CT* __restrict__ rc, const int* skip) {
+  pdl_trigger();
+  pdl_wait();
   if (*skip) return;
   int J = blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= nc) return;
@@ -141,6 +150,8 @@ __global__ void __launch_bounds__(AMG_BLOCK) k_restrict(int nc, const int32_t* _
 template <typename VT, typename CT>
 __global__ void __launch_bounds__(AMG_BLOCK) k_prolong(int n, const int32_t* __restrict__ agg, const CT* __restrict__ zc,
                                                        VT* __restrict__ z, const int* skip) {
+  pdl_trigger();
+  pdl_wait();
   if (*skip) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -149,6 +160,8 @@ __global__ void __launch_bounds__(AMG_BLOCK) k_prolong(int n, const int32_t* __r
 
 template <typename VT, typename OT>
 __global__ void k_copy(int n, const VT* __restrict__ a, OT* __restrict__ b, const int* skip) {
+  pdl_trigger();
+  pdl_wait();
   if (*skip) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (OT)a[i];
@@ -156,6 +169,8 @@ __global__ void k_copy(int n, const VT* __restrict__ a, OT* __restrict__ b, cons
 
 template <typename VT>
 __global__ void k_add(int n, const VT* __restrict__ x, VT* __restrict__ y, const int* skip) {
+  pdl_trigger();
+  pdl_wait();
   if (*skip) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] += x[i];
@@ -163,6 +178,8 @@ __global__ void k_add(int n, const VT* __restrict__ x, VT* __restrict__ y, const
 
 template <typename VT>
 __global__ void k_zero(int n, VT* __restrict__ a, const int* skip) {
+  pdl_trigger();
+  pdl_wait();
   if (*skip) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] = (VT)0;
@@ -233,6 +250,8 @@ __global__ void __launch_bounds__(R) k_fcg_resid(int n, const int32_t* __restric
                                                  const double* __restrict__ v, const double* __restrict__ b,
                                                  const double* __restrict__ u, double* __restrict__ r, FcgState* st,
                                                  double* partial, unsigned* counter) {
+  pdl_trigger();
+  pdl_wait();
   if (MODE == RES_TRUE && (st->done || !st->need_true)) return;
   __shared__ __align__(16) TileSmem<double> sm;
   __shared__ double red[64];
@@ -261,6 +280,8 @@ __global__ void __launch_bounds__(R) k_fcg_spmv_dots(int n, const int32_t* __res
                                                      const double* __restrict__ r, const double* __restrict__ q,
                                                      double* __restrict__ vout, FcgState* st, double* partial,
                                                      unsigned* counter) {
+  pdl_trigger();
+  pdl_wait();
   if (st->done) return;
   __shared__ __align__(16) TileSmem<double> sm;
   __shared__ double red[96];
@@ -306,6 +327,8 @@ __global__ void __launch_bounds__(AMG_BLOCK) k_fcg_axpy(int n, const double* __r
                                                         double* __restrict__ d, double* __restrict__ q,
                                                         double* __restrict__ u, double* __restrict__ r, FcgState* st,
                                                         double* partial, unsigned* counter) {
+  pdl_trigger();
+  pdl_wait();
   if (st->done) return;
   __shared__ double red[32];
   const bool first = st->it == 0;
@@ -342,6 +365,26 @@ __global__ void __launch_bounds__(AMG_BLOCK) k_fcg_axpy(int n, const double* __r
     st->done = 1;
   }
 }
+
+// AMG_PDL: 0 off, 1 every solve-phase kernel, 2 the V-cycle kernels only (default:
+// measured best; on the outer reduction kernels it costs more than it saves)
+static int pdl_mode() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = getenv("AMG_PDL");
+    on = e ? atoi(e) : 2;
+  }
+  return on;
+}
+static thread_local bool g_outer_launch = false;  // set while the outer FCG kernels are launched
+bool amg_pdl_enabled() {
+  const int m = pdl_mode();
+  return m == 1 || (m == 2 && !g_outer_launch);
+}
+struct OuterLaunch {
+  OuterLaunch() { g_outer_launch = true; }
+  ~OuterLaunch() { g_outer_launch = false; }
+};
 
 int amg_num_sms() {
   static int sms = 0;
@@ -394,7 +437,7 @@ static void launch_sweep(cudaStream_t s, const Level& L, const MT* vals, const V
     return;
   }
   const int nb = (L.n + R - 1) / R;
-  DISPATCH_R(R, (k_sweep<TR, MT, VT, OT><<<nb, TR, 0, s>>>(L.n, L.rp, L.ci, vals, dinv, r, z, out, skip)));
+  DISPATCH_R(R, (amg_launch(k_sweep<TR, MT, VT, OT>, dim3(nb), dim3(TR), 0, s, L.n, L.rp, L.ci, vals, dinv, r, z, out, skip)));
 }
 
 template <typename MT, typename VT>
@@ -407,11 +450,12 @@ static void launch_resid(cudaStream_t s, const Level& L, const MT* vals, const V
     return;
   }
   const int nb = (L.n + R - 1) / R;
-  DISPATCH_R(R, (k_resid<TR, MT, VT><<<nb, TR, 0, s>>>(L.n, L.rp, L.ci, vals, r, z, t, skip)));
+  DISPATCH_R(R, (amg_launch(k_resid<TR, MT, VT>, dim3(nb), dim3(TR), 0, s, L.n, L.rp, L.ci, vals, r, z, t, skip)));
 }
 
 // outer kernels on level 0 (FP64 values)
 static void launch_dots(amg_handle* h, cudaStream_t s) {
+  OuterLaunch outer;
   Level& L = h->L[0];
   if (L.piped) {
     RowArgs<double, double, double> a{L.n, L.rp, L.ci, L.v, h->w, nullptr, h->r, nullptr, h->q, h->v,
@@ -425,6 +469,7 @@ static void launch_dots(amg_handle* h, cudaStream_t s) {
 
 template <int MODE>
 static void launch_fcg_resid(amg_handle* h, cudaStream_t s) {
+  OuterLaunch outer;
   Level& L = h->L[0];
   constexpr int PM = MODE == RES_INIT ? PM_RINIT : (MODE == RES_TRUE ? PM_RTRUE : PM_RNORM);
   if (L.piped) {
@@ -472,12 +517,12 @@ static double* rec_coarse(VRec& R, int k, const double* r, double* final_out) {
   double* cur = za;
   if (sweeps <= 0) {
     double* o = final_out ? final_out : za;
-    k_zero<double><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, o, R.skip);
+    amg_launch(k_zero<double>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, o, R.skip);
     R.add(8.0 * n);
     return o;
   }
   double* o = (sweeps == 1 && final_out) ? final_out : za;
-  k_first<double, double><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, L.dinv, r, nullptr, o, R.skip);
+  amg_launch(k_first<double, double>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.dinv, r, nullptr, o, R.skip);
   R.add(24.0 * n);
   cur = o;
   for (int sw = 1; sw < sweeps; ++sw) {
@@ -548,41 +593,41 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
   if (k + 1 == h->kb) {  // the bottom levels in one launch
     const double sc = vec_bytes(C);
     if (k + 1 == h->nl - 1) {
-      k_restrict<VT, double><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, L.mptr, L.mem, t, (double*)C.r, R.skip);
+      amg_launch(k_restrict<VT, double>, dim3(ncb), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (double*)C.r, R.skip);
       R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 8.0 * nc);
       rec_bottom(R);
-      k_prolong<VT, double><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, L.agg, (const double*)C.za, z, R.skip);
+      amg_launch(k_prolong<VT, double>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, (const double*)C.za, z, R.skip);
     } else {
-      k_restrict<VT, VT><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip);
+      amg_launch(k_restrict<VT, VT>, dim3(ncb), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip);
       R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc);
       rec_bottom(R);
-      k_prolong<VT, VT><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, L.agg, (const VT*)C.za, z, R.skip);
+      amg_launch(k_prolong<VT, VT>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, (const VT*)C.za, z, R.skip);
     }
     R.add(4.0 * n + sc * nc + 2.0 * sx * n);
     return;
   }
   const bool wcyc = h->p.cycle == 2;
   if (k + 1 == h->nl - 1) {  // coarsest: FP64
-    k_restrict<VT, double><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, L.mptr, L.mem, t, (double*)C.r, R.skip);
+    amg_launch(k_restrict<VT, double>, dim3(ncb), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (double*)C.r, R.skip);
     R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 8.0 * nc);
     double* zc = rec_coarse(R, k + 1, (const double*)C.r, nullptr);
     if (wcyc) {  // W-cycle: e = z_c;  r2 = r_c - A_c e;  e += B_c r2
       double* e = (double*)C.e;
       double* r2 = (double*)C.r2;
-      k_copy<double, double><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, zc, e, R.skip);
+      amg_launch(k_copy<double, double>, dim3(ncb), dim3(AMG_BLOCK), 0, R.s, C.n, zc, e, R.skip);
       launch_resid<double, double>(R.s, C, C.v, (const double*)C.r, e, r2, R.skip, h->dev_flags, h->stages);
       double* zc2 = rec_coarse(R, k + 1, r2, nullptr);
-      k_add<double><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, zc2, e, R.skip);
+      amg_launch(k_add<double>, dim3(ncb), dim3(AMG_BLOCK), 0, R.s, C.n, zc2, e, R.skip);
       R.add(16.0 * nc);
       R.add(row_pass(C, 8.0) + 24.0 * nc);
       R.add(24.0 * nc);
       zc = e;
     }
-    k_prolong<VT, double><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, L.agg, zc, z, R.skip);
+    amg_launch(k_prolong<VT, double>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip);
     R.add(4.0 * n + 8.0 * nc + 2.0 * sx * n);
   } else {
     const double sc = vec_bytes(C);
-    k_restrict<VT, VT><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip);
+    amg_launch(k_restrict<VT, VT>, dim3(ncb), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip);
     R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc);
     VT* zc;
     if (C.lowp) zc = (VT*)rec_level<float, float, float>(R, k + 1, (const float*)C.r, nullptr);
@@ -590,7 +635,7 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
     if (wcyc) {
       VT* e = (VT*)C.e;
       VT* r2 = (VT*)C.r2;
-      k_copy<VT, VT><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, zc, e, R.skip);
+      amg_launch(k_copy<VT, VT>, dim3(ncb), dim3(AMG_BLOCK), 0, R.s, C.n, zc, e, R.skip);
       if (C.lowp) launch_resid<float, float>(R.s, C, C.vf, (const float*)C.r, (const float*)e, (float*)r2, R.skip,
                                              h->dev_flags, h->stages);
       else launch_resid<double, double>(R.s, C, C.v, (const double*)C.r, (const double*)e, (double*)r2, R.skip,
@@ -598,13 +643,13 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
       VT* zc2;
       if (C.lowp) zc2 = (VT*)rec_level<float, float, float>(R, k + 1, (const float*)r2, nullptr);
       else zc2 = (VT*)rec_level<double, double, double>(R, k + 1, (const double*)r2, nullptr);
-      k_add<VT><<<ncb, AMG_BLOCK, 0, R.s>>>(C.n, zc2, e, R.skip);
+      amg_launch(k_add<VT>, dim3(ncb), dim3(AMG_BLOCK), 0, R.s, C.n, zc2, e, R.skip);
       R.add(2.0 * sc * nc);
       R.add(row_pass(C, val_bytes(C)) + 3.0 * sc * nc);
       R.add(3.0 * sc * nc);
       zc = e;
     }
-    k_prolong<VT, VT><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, L.agg, zc, z, R.skip);
+    amg_launch(k_prolong<VT, VT>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip);
     R.add(4.0 * n + sc * nc + 2.0 * sx * n);
   }
 }
@@ -638,7 +683,7 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out) {
   // pre-smoothing from zero
   VT* cur = za;
   if (h->p.pre_sweeps > 0) {
-    k_first<RT, VT><<<nb, AMG_BLOCK, 0, R.s>>>(L.n, dinv, rin, rcopy, za, R.skip);
+    amg_launch(k_first<RT, VT>, dim3(nb), dim3(AMG_BLOCK), 0, R.s, L.n, dinv, rin, rcopy, za, R.skip);
     R.add(sr * n + 2.0 * sx * n + rc_bytes);
     for (int sw = 1; sw < h->p.pre_sweeps; ++sw) {
       VT* nxt = cur == za ? zb : za;
@@ -648,10 +693,10 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out) {
     }
   } else {
     if (rcopy) {
-      k_copy<RT, VT><<<nb, AMG_BLOCK, 0, R.s>>>(L.n, rin, rcopy, R.skip);
+      amg_launch(k_copy<RT, VT>, dim3(nb), dim3(AMG_BLOCK), 0, R.s, L.n, rin, rcopy, R.skip);
       R.add(sr * n + rc_bytes);
     }
-    k_zero<VT><<<nb, AMG_BLOCK, 0, R.s>>>(L.n, za, R.skip);
+    amg_launch(k_zero<VT>, dim3(nb), dim3(AMG_BLOCK), 0, R.s, L.n, za, R.skip);
     R.add(sx * n);
   }
   // residual, restriction, coarse correction, prolongation
@@ -661,7 +706,7 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out) {
   // post-smoothing
   const int post = h->p.post_sweeps;
   if (post == 0 && final_out) {
-    k_copy<VT, double><<<nb, AMG_BLOCK, 0, R.s>>>(L.n, cur, final_out, R.skip);
+    amg_launch(k_copy<VT, double>, dim3(nb), dim3(AMG_BLOCK), 0, R.s, L.n, cur, final_out, R.skip);
     R.add(sx * n + 8.0 * n);
     return nullptr;
   }
@@ -706,12 +751,16 @@ static void record_iteration(VRec& R, bool precond) {
   R.skip = skip;
   if (precond) record_vcycle(R, h->r, h->w);
   else {
-    k_copy<double, double><<<amg_blocks(L.n), AMG_BLOCK, 0, R.s>>>(L.n, h->r, h->w, skip);
+    amg_launch(k_copy<double, double>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, h->r, h->w, skip);
     R.add(16.0 * L.n);
   }
   launch_dots(h, R.s);
   R.add(bytes_spmv_dots(L));
-  k_fcg_axpy<<<h->ax_grid, AMG_BLOCK, 0, R.s>>>(L.n, h->w, h->v, h->d, h->q, h->u, h->r, st, h->partial, h->counter);
+  {
+    OuterLaunch outer;
+    amg_launch(k_fcg_axpy, dim3(h->ax_grid), dim3(AMG_BLOCK), 0, R.s, L.n, h->w, h->v, h->d, h->q, h->u, h->r, st,
+               h->partial, h->counter);
+  }
   R.add(bytes_axpy(L));
   // the true-residual check moves data only once per solve (at convergence)
   launch_fcg_resid<RES_TRUE>(h, R.s);
@@ -1048,13 +1097,13 @@ static amg_status launch_one(amg_handle* h, int which, int k) {
       Level& C = h->L[k + 1];
       bool ccoarse = (k + 1 == h->nl - 1);
       if (which == 2) {
-        if (!L.lowp) k_restrict<double, double><<<amg_blocks(C.n), AMG_BLOCK, 0, s>>>(C.n, L.mptr, L.mem, (double*)L.t, (double*)C.r, skip);
-        else if (ccoarse) k_restrict<float, double><<<amg_blocks(C.n), AMG_BLOCK, 0, s>>>(C.n, L.mptr, L.mem, (float*)L.t, (double*)C.r, skip);
-        else k_restrict<float, float><<<amg_blocks(C.n), AMG_BLOCK, 0, s>>>(C.n, L.mptr, L.mem, (float*)L.t, (float*)C.r, skip);
+        if (!L.lowp) amg_launch(k_restrict<double, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (double*)L.t, (double*)C.r, skip);
+        else if (ccoarse) amg_launch(k_restrict<float, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (float*)L.t, (double*)C.r, skip);
+        else amg_launch(k_restrict<float, float>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (float*)L.t, (float*)C.r, skip);
       } else {
-        if (!L.lowp) k_prolong<double, double><<<amg_blocks(L.n), AMG_BLOCK, 0, s>>>(L.n, L.agg, (double*)C.za, (double*)L.za, skip);
-        else if (ccoarse) k_prolong<float, double><<<amg_blocks(L.n), AMG_BLOCK, 0, s>>>(L.n, L.agg, (double*)C.za, (float*)L.za, skip);
-        else k_prolong<float, float><<<amg_blocks(L.n), AMG_BLOCK, 0, s>>>(L.n, L.agg, (float*)C.za, (float*)L.za, skip);
+        if (!L.lowp) amg_launch(k_prolong<double, double>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (double*)C.za, (double*)L.za, skip);
+        else if (ccoarse) amg_launch(k_prolong<float, double>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (double*)C.za, (float*)L.za, skip);
+        else amg_launch(k_prolong<float, float>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (float*)C.za, (float*)L.za, skip);
       }
       break;
     }
@@ -1064,7 +1113,7 @@ static amg_status launch_one(amg_handle* h, int which, int k) {
       break;
     case 5:
       if (k != 0) return amg_fail(h, AMG_ERR_INVALID_ARG, "outer kernels run on level 0");
-      k_fcg_axpy<<<h->ax_grid, AMG_BLOCK, 0, s>>>(L.n, h->w, h->v, h->d, h->q, h->u, h->r, h->st, h->partial, h->counter);
+      amg_launch(k_fcg_axpy, dim3(h->ax_grid), dim3(AMG_BLOCK), 0, s, L.n, h->w, h->v, h->d, h->q, h->u, h->r, h->st, h->partial, h->counter);
       break;
     default:
       return amg_fail(h, AMG_ERR_INVALID_ARG, "unknown kernel id %d", which);
