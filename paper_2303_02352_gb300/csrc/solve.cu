@@ -74,6 +74,11 @@ __device__ __forceinline__ AT tile_row_dot(TileSmem<MT>& sm, int row0, int row1,
   return s;
 }
 
+// Elementwise kernels handle EW elements per thread, strided by the whole grid
+// (every load stays coalesced; EW independent loads are in flight per thread).
+#define EW 4
+static inline int ew_blocks(int64_t n) { return (int)((n + (int64_t)AMG_BLOCK * EW - 1) / ((int64_t)AMG_BLOCK * EW)); }
+
 // first sweep from z = 0: z = D r (the level input may be FP64 and the level
 // float: then the rounded input is also kept in rcopy for the later sweeps)
 template <typename RT, typename VT>
@@ -82,11 +87,24 @@ __global__ void __launch_bounds__(AMG_BLOCK) k_first(int n, const VT* __restrict
   pdl_trigger();
   pdl_wait();
   if (*skip) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  VT ri = (VT)r[i];
-  if (rcopy) rcopy[i] = ri;
-  z[i] = dinv[i] * ri;
+  const int T = gridDim.x * blockDim.x, i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  VT ri[EW], di[EW];
+#pragma unroll
+  for (int u = 0; u < EW; ++u) {
+    const int i = i0 + u * T;
+    if (i < n) {
+      ri[u] = (VT)r[i];
+      di[u] = dinv[i];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < EW; ++u) {
+    const int i = i0 + u * T;
+    if (i < n) {
+      if (rcopy) rcopy[i] = ri[u];
+      z[i] = di[u] * ri[u];
+    }
+  }
 }
 
 // l1-Jacobi sweep z_out = z + D (r - A z)
@@ -132,14 +150,16 @@ __global__ void __launch_bounds__(R) k_spmv(int n, const int32_t* __restrict__ r
   if (row < row1) y[row] = s;
 }
 
-// r_c[J] = sum over the members i of aggregate J (ascending) of t_i
+// r_c[J] = sum over the members i of aggregate J (ascending) of t_i (one
+// coarse row per thread: the member loads of a row depend on each other, so
+// more rows per thread would only serialise them)
 template <typename VT, typename CT>
 __global__ void __launch_bounds__(AMG_BLOCK) k_restrict(int nc, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
                                                         const VT* __restrict__ t, CT* __restrict__ rc, const int* skip) {
   pdl_trigger();
   pdl_wait();
   if (*skip) return;
-  int J = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= nc) return;
   VT s = 0;
   for (int m = mptr[J]; m < mptr[J + 1]; ++m) s += t[mem[m]];
@@ -153,9 +173,23 @@ __global__ void __launch_bounds__(AMG_BLOCK) k_prolong(int n, const int32_t* __r
   pdl_trigger();
   pdl_wait();
   if (*skip) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  z[i] += (VT)zc[agg[i]];
+  const int T = gridDim.x * blockDim.x, i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  int a[EW];
+  VT zz[EW];
+#pragma unroll
+  for (int u = 0; u < EW; ++u) {
+    const int i = i0 + u * T;
+    a[u] = 0;
+    if (i < n) {
+      a[u] = agg[i];
+      zz[u] = z[i];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < EW; ++u) {
+    const int i = i0 + u * T;
+    if (i < n) z[i] = zz[u] + (VT)zc[a[u]];
+  }
 }
 
 template <typename VT, typename OT>
@@ -163,8 +197,12 @@ __global__ void k_copy(int n, const VT* __restrict__ a, OT* __restrict__ b, cons
   pdl_trigger();
   pdl_wait();
   if (*skip) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = (OT)a[i];
+  const int T = gridDim.x * blockDim.x, i0 = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < EW; ++u) {
+    const int i = i0 + u * T;
+    if (i < n) b[i] = (OT)a[i];
+  }
 }
 
 template <typename VT>
@@ -172,8 +210,12 @@ __global__ void k_add(int n, const VT* __restrict__ x, VT* __restrict__ y, const
   pdl_trigger();
   pdl_wait();
   if (*skip) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] += x[i];
+  const int T = gridDim.x * blockDim.x, i0 = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < EW; ++u) {
+    const int i = i0 + u * T;
+    if (i < n) y[i] += x[i];
+  }
 }
 
 template <typename VT>
@@ -181,8 +223,12 @@ __global__ void k_zero(int n, VT* __restrict__ a, const int* skip) {
   pdl_trigger();
   pdl_wait();
   if (*skip) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) a[i] = (VT)0;
+  const int T = gridDim.x * blockDim.x, i0 = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < EW; ++u) {
+    const int i = i0 + u * T;
+    if (i < n) a[i] = (VT)0;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -517,12 +563,12 @@ static double* rec_coarse(VRec& R, int k, const double* r, double* final_out) {
   double* cur = za;
   if (sweeps <= 0) {
     double* o = final_out ? final_out : za;
-    amg_launch(k_zero<double>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, o, R.skip);
+    amg_launch(k_zero<double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, o, R.skip);
     R.add(8.0 * n);
     return o;
   }
   double* o = (sweeps == 1 && final_out) ? final_out : za;
-  amg_launch(k_first<double, double>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.dinv, r, nullptr, o, R.skip);
+  amg_launch(k_first<double, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.dinv, r, nullptr, o, R.skip);
   R.add(24.0 * n);
   cur = o;
   for (int sw = 1; sw < sweeps; ++sw) {
@@ -593,41 +639,41 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
   if (k + 1 == h->kb) {  // the bottom levels in one launch
     const double sc = vec_bytes(C);
     if (k + 1 == h->nl - 1) {
-      amg_launch(k_restrict<VT, double>, dim3(ncb), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (double*)C.r, R.skip);
+      amg_launch(k_restrict<VT, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (double*)C.r, R.skip);
       R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 8.0 * nc);
       rec_bottom(R);
-      amg_launch(k_prolong<VT, double>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, (const double*)C.za, z, R.skip);
+      amg_launch(k_prolong<VT, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, (const double*)C.za, z, R.skip);
     } else {
-      amg_launch(k_restrict<VT, VT>, dim3(ncb), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip);
+      amg_launch(k_restrict<VT, VT>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip);
       R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc);
       rec_bottom(R);
-      amg_launch(k_prolong<VT, VT>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, (const VT*)C.za, z, R.skip);
+      amg_launch(k_prolong<VT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, (const VT*)C.za, z, R.skip);
     }
     R.add(4.0 * n + sc * nc + 2.0 * sx * n);
     return;
   }
   const bool wcyc = h->p.cycle == 2;
   if (k + 1 == h->nl - 1) {  // coarsest: FP64
-    amg_launch(k_restrict<VT, double>, dim3(ncb), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (double*)C.r, R.skip);
+    amg_launch(k_restrict<VT, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (double*)C.r, R.skip);
     R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 8.0 * nc);
     double* zc = rec_coarse(R, k + 1, (const double*)C.r, nullptr);
     if (wcyc) {  // W-cycle: e = z_c;  r2 = r_c - A_c e;  e += B_c r2
       double* e = (double*)C.e;
       double* r2 = (double*)C.r2;
-      amg_launch(k_copy<double, double>, dim3(ncb), dim3(AMG_BLOCK), 0, R.s, C.n, zc, e, R.skip);
+      amg_launch(k_copy<double, double>, dim3(ew_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, zc, e, R.skip);
       launch_resid<double, double>(R.s, C, C.v, (const double*)C.r, e, r2, R.skip, h->dev_flags, h->stages);
       double* zc2 = rec_coarse(R, k + 1, r2, nullptr);
-      amg_launch(k_add<double>, dim3(ncb), dim3(AMG_BLOCK), 0, R.s, C.n, zc2, e, R.skip);
+      amg_launch(k_add<double>, dim3(ew_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, zc2, e, R.skip);
       R.add(16.0 * nc);
       R.add(row_pass(C, 8.0) + 24.0 * nc);
       R.add(24.0 * nc);
       zc = e;
     }
-    amg_launch(k_prolong<VT, double>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip);
+    amg_launch(k_prolong<VT, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip);
     R.add(4.0 * n + 8.0 * nc + 2.0 * sx * n);
   } else {
     const double sc = vec_bytes(C);
-    amg_launch(k_restrict<VT, VT>, dim3(ncb), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip);
+    amg_launch(k_restrict<VT, VT>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip);
     R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc);
     VT* zc;
     if (C.lowp) zc = (VT*)rec_level<float, float, float>(R, k + 1, (const float*)C.r, nullptr);
@@ -635,7 +681,7 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
     if (wcyc) {
       VT* e = (VT*)C.e;
       VT* r2 = (VT*)C.r2;
-      amg_launch(k_copy<VT, VT>, dim3(ncb), dim3(AMG_BLOCK), 0, R.s, C.n, zc, e, R.skip);
+      amg_launch(k_copy<VT, VT>, dim3(ew_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, zc, e, R.skip);
       if (C.lowp) launch_resid<float, float>(R.s, C, C.vf, (const float*)C.r, (const float*)e, (float*)r2, R.skip,
                                              h->dev_flags, h->stages);
       else launch_resid<double, double>(R.s, C, C.v, (const double*)C.r, (const double*)e, (double*)r2, R.skip,
@@ -643,13 +689,13 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
       VT* zc2;
       if (C.lowp) zc2 = (VT*)rec_level<float, float, float>(R, k + 1, (const float*)r2, nullptr);
       else zc2 = (VT*)rec_level<double, double, double>(R, k + 1, (const double*)r2, nullptr);
-      amg_launch(k_add<VT>, dim3(ncb), dim3(AMG_BLOCK), 0, R.s, C.n, zc2, e, R.skip);
+      amg_launch(k_add<VT>, dim3(ew_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, zc2, e, R.skip);
       R.add(2.0 * sc * nc);
       R.add(row_pass(C, val_bytes(C)) + 3.0 * sc * nc);
       R.add(3.0 * sc * nc);
       zc = e;
     }
-    amg_launch(k_prolong<VT, VT>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip);
+    amg_launch(k_prolong<VT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip);
     R.add(4.0 * n + sc * nc + 2.0 * sx * n);
   }
 }
@@ -683,7 +729,7 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out) {
   // pre-smoothing from zero
   VT* cur = za;
   if (h->p.pre_sweeps > 0) {
-    amg_launch(k_first<RT, VT>, dim3(nb), dim3(AMG_BLOCK), 0, R.s, L.n, dinv, rin, rcopy, za, R.skip);
+    amg_launch(k_first<RT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, dinv, rin, rcopy, za, R.skip);
     R.add(sr * n + 2.0 * sx * n + rc_bytes);
     for (int sw = 1; sw < h->p.pre_sweeps; ++sw) {
       VT* nxt = cur == za ? zb : za;
@@ -693,10 +739,10 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out) {
     }
   } else {
     if (rcopy) {
-      amg_launch(k_copy<RT, VT>, dim3(nb), dim3(AMG_BLOCK), 0, R.s, L.n, rin, rcopy, R.skip);
+      amg_launch(k_copy<RT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, rin, rcopy, R.skip);
       R.add(sr * n + rc_bytes);
     }
-    amg_launch(k_zero<VT>, dim3(nb), dim3(AMG_BLOCK), 0, R.s, L.n, za, R.skip);
+    amg_launch(k_zero<VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, za, R.skip);
     R.add(sx * n);
   }
   // residual, restriction, coarse correction, prolongation
@@ -706,7 +752,7 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out) {
   // post-smoothing
   const int post = h->p.post_sweeps;
   if (post == 0 && final_out) {
-    amg_launch(k_copy<VT, double>, dim3(nb), dim3(AMG_BLOCK), 0, R.s, L.n, cur, final_out, R.skip);
+    amg_launch(k_copy<VT, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, cur, final_out, R.skip);
     R.add(sx * n + 8.0 * n);
     return nullptr;
   }
@@ -751,7 +797,7 @@ static void record_iteration(VRec& R, bool precond) {
   R.skip = skip;
   if (precond) record_vcycle(R, h->r, h->w);
   else {
-    amg_launch(k_copy<double, double>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, h->r, h->w, skip);
+    amg_launch(k_copy<double, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, h->r, h->w, skip);
     R.add(16.0 * L.n);
   }
   launch_dots(h, R.s);
@@ -1101,9 +1147,9 @@ static amg_status launch_one(amg_handle* h, int which, int k) {
         else if (ccoarse) amg_launch(k_restrict<float, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (float*)L.t, (double*)C.r, skip);
         else amg_launch(k_restrict<float, float>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (float*)L.t, (float*)C.r, skip);
       } else {
-        if (!L.lowp) amg_launch(k_prolong<double, double>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (double*)C.za, (double*)L.za, skip);
-        else if (ccoarse) amg_launch(k_prolong<float, double>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (double*)C.za, (float*)L.za, skip);
-        else amg_launch(k_prolong<float, float>, dim3(amg_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (float*)C.za, (float*)L.za, skip);
+        if (!L.lowp) amg_launch(k_prolong<double, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (double*)C.za, (double*)L.za, skip);
+        else if (ccoarse) amg_launch(k_prolong<float, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (double*)C.za, (float*)L.za, skip);
+        else amg_launch(k_prolong<float, float>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (float*)C.za, (float*)L.za, skip);
       }
       break;
     }

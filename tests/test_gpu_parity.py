@@ -345,3 +345,61 @@ def test_wcycle_parity(prec):
     assert rg["iters"] <= G(A, precision=prec).pcg_solve(b)["iters"]
     info = g.info()
     assert info["setup_match_ms"] > 0 and info["setup_galerkin_ms"] > 0
+
+
+# ---------------------------------------------------------------------------
+# full-size 27-point log-normal workload (2.1M rows, 55.7M nonzeros): checks
+# that hold at any size, plus sampled coarse rows recomputed from level 0
+
+
+@pytest.fixture(scope="module")
+def big27():
+    A, b, _ = W.config("diffusion27_128")
+    return A, b, G(A)
+
+
+def test_full_size_27pt_hierarchy_properties(big27):
+    A, b, g = big27
+    info = g.info()
+    assert info["n"][0] == 128 ** 3 and info["nnz"][0] == 382 ** 3
+    n0, n1 = info["n"][0], info["n"][1]
+    agg = g.aggregates(0)
+    assert agg.min() == 0 and agg.max() == n1 - 1
+    sizes = np.bincount(agg, minlength=n1)
+    assert sizes.min() >= 1 and sizes.max() <= 8
+    # sampled coarse rows of level 1 against P^T A P computed directly from level 0
+    rp1, ci1, v1 = g.level_csr(1)
+    rng = np.random.default_rng(0)
+    members = np.argsort(agg, kind="stable")
+    starts = np.concatenate([[0], np.cumsum(sizes)])
+    for I in rng.choice(n1, size=200, replace=False):
+        acc = {}
+        for i in members[starts[I]:starts[I + 1]]:
+            for p in range(A.row_ptr[i], A.row_ptr[i + 1]):
+                J = int(agg[A.col_idx[p]])
+                acc[J] = acc.get(J, 0.0) + A.val[p]
+        cols = np.array(sorted(acc))
+        vals = np.array([acc[J] for J in cols])
+        assert np.array_equal(ci1[rp1[I]:rp1[I + 1]], cols)
+        assert np.allclose(v1[rp1[I]:rp1[I + 1]], vals, rtol=1e-12, atol=1e-12 * np.abs(vals).max())
+    # bitwise symmetric coarse operators on every level
+    for k in range(1, info["num_levels"]):
+        rp, ci, v = g.level_csr(k)
+        S = __import__("scipy.sparse", fromlist=["csr_matrix"]).csr_matrix((v, ci, rp))
+        assert abs(S - S.T).max() == 0.0
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_full_size_27pt_vcycle_symmetry_and_solves(big27, prec):
+    A, b, g64 = big27
+    g = g64 if prec == 0 else G(A, precision=prec)
+    x = W.random_vector(A.n, 21)
+    y = W.random_vector(A.n, 22)
+    bx, by = g.vcycle(x).cpu().numpy(), g.vcycle(y).cpu().numpy()
+    asym = abs(x @ by - y @ bx) / (np.linalg.norm(x) * np.linalg.norm(by))
+    assert asym < (1e-13 if prec == 0 else 1e-5)
+    res = g.pcg_solve(b)
+    assert res["status"] == 0 and res["true_rel_res"] < 1e-6
+    xs = W.exact_solution("diffusion27_128", A.n)
+    err = np.linalg.norm(res["x"].cpu().numpy() - xs) / np.linalg.norm(xs)
+    assert err < 1e-3
