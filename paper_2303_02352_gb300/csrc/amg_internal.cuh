@@ -152,16 +152,24 @@ void amg_release(amg_handle* h, void* p);     // frees one allocation of the han
 
 static inline int amg_blocks(int64_t threads) { return (int)((threads + AMG_BLOCK - 1) / AMG_BLOCK); }
 
-// bytes of one pipeline stage of the row kernels (values + column indices)
+// consumer threads of the pipelined row kernels and the bytes of one pipeline
+// stage (values + column indices), sized per value type so that a tile of a
+// 7-point stencil fits with little slack
+#ifndef PIPE_CONSUMERS
+#define PIPE_CONSUMERS 256
+#endif
+#ifndef PIPE_STAGE_SCALE
+#define PIPE_STAGE_SCALE 1  // stages are 24/16/12 KB divided by this (FP64/FP32/BF16 values)
+#endif
 __host__ __device__ constexpr int amg_pipe_tile_bytes(int value_bytes) {
-  return value_bytes >= 8 ? 24576 : (value_bytes >= 4 ? 16384 : 12288);
+  return (value_bytes >= 8 ? 24576 : (value_bytes >= 4 ? 16384 : 12288)) / PIPE_STAGE_SCALE;
 }
 
 // tile height of the row kernels: the largest power of two R <= 256 rows
 // (at least rmin) whose longest-row bound fits one pipeline stage
 static inline int amg_tile_rows(int maxrow, int value_bytes, int rmin = 32) {
   const int cap = amg_pipe_tile_bytes(value_bytes) / (value_bytes + 4);
-  int R = 256;
+  int R = PIPE_CONSUMERS;
   while (R > rmin && (int64_t)R * maxrow > cap) R /= 2;
   return R;
 }

@@ -20,8 +20,9 @@
 #define PIPE_WAIT_NS 2000000000ull  // 2 s: a copy of at most 24 KB never takes this long
 
 // stage capacity (values + column indices): sized per value type so that a
-// 256-row tile of a 7-point stencil fits with little slack (smaller stages mean
-// more resident blocks per multiprocessor, which is what the row kernels need)
+// PIPE_CONSUMERS-row tile of a 7-point stencil fits with little slack (smaller
+// stages mean more resident blocks per multiprocessor, which is what the row
+// kernels need)
 template <typename MT>
 struct PipeTile {
   static constexpr int VE = 16 / (int)sizeof(MT);
@@ -121,12 +122,12 @@ __device__ __forceinline__ bool mbar_wait_warp(unsigned long long* bar, uint32_t
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
 
-#define PIPE_CONSUMERS 256
 
-// Warp-specialised persistent row kernel: 8 consumer warps and one producer
-// warp.  A tile holds R = 256 / TPR rows; TPR threads share a row (entries
-// strided by TPR, summed with shuffles), so that long rows still keep 256
-// threads busy per tile; TPR = 1 for short rows (one thread per row).  Per stage a "full" barrier (the producer's
+// Warp-specialised persistent row kernel: PIPE_CONSUMERS / 32 consumer warps
+// (8 by default) and one producer warp.  A tile holds R = PIPE_CONSUMERS / TPR
+// rows; TPR threads share a row (entries strided by TPR, summed with shuffles),
+// so that long rows still keep every consumer busy per tile; TPR = 1 for short
+// rows (one thread per row).  Per stage a "full" barrier (the producer's
 // expect_tx plus the bytes of the two bulk copies) and an "empty" barrier (one
 // arrival per consumer warp once it has read the stage).  No block-wide
 // barrier inside the tile loop: warps drift up to S tiles apart.

@@ -786,8 +786,8 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
     L.R = amg_tile_rows(mr, vb);
     const bool big = L.n >= h->small_rows;
     // pipelined kernels: tile heights down to 8 rows (32 threads per row)
-    const int Rp = std::min(amg_tile_rows(mr, vb, 8), 256 / std::max(1, h->min_tpr));
-    const int Rpd = std::min(amg_tile_rows(mr, 8, 8), 256 / std::max(1, h->min_tpr));
+    const int Rp = std::min(amg_tile_rows(mr, vb, PIPE_CONSUMERS / 32), PIPE_CONSUMERS / std::max(1, h->min_tpr));
+    const int Rpd = std::min(amg_tile_rows(mr, 8, PIPE_CONSUMERS / 32), PIPE_CONSUMERS / std::max(1, h->min_tpr));
     L.piped = h->use_pipe && (int64_t)Rpd * mr <= amg_pipe_tile_bytes(8) / 12;
     L.pipe = h->use_pipe && big && (int64_t)Rp * mr <= amg_pipe_tile_bytes(vb) / (vb + 4);
     if (L.piped) L.Rd = Rpd;

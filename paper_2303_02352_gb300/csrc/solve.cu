@@ -595,23 +595,45 @@ static void rec_bottom(VRec& R) {
   a.post = h->p.post_sweeps;
   a.csweeps = h->p.coarse_sweeps;
   a.skip = R.skip;
+  a.r_in = h->L[kb].r;
+  a.z_out = h->L[kb].za;
+  const bool lowp = h->L[kb].lowp;
   double bytes = 0.0;
+  // layout for a cluster of cs blocks: chunk = next power of two >= ceil(n / cs)
+  auto layout = [&](int cs) {
+    int off = 0;
+    for (int j = 0; j < a.nb; ++j) {
+      Level& L = h->L[kb + j];
+      const bool coarsest = kb + j == h->nl - 1;
+      BotLevel& B = a.L[j];
+      const int per = (L.n + cs - 1) / cs;
+      int sh = 0;
+      while ((1 << sh) < per) ++sh;
+      const int es = coarsest ? 8 : (L.lowp ? 4 : 8);
+      const int vb = (((1 << sh) * es + 15) / 16) * 16;
+      B.n = L.n;
+      B.shift = sh;
+      B.rp = L.rp;
+      B.ci = L.ci;
+      B.v = L.lowp ? (const void*)L.vf : (const void*)L.v;
+      B.dinv = L.lowp ? (const void*)L.dinvf : (const void*)L.dinv;
+      B.agg = coarsest ? nullptr : L.agg;
+      B.mptr = coarsest ? nullptr : L.mptr;
+      B.mem = coarsest ? nullptr : L.mem;
+      B.off_r = off;
+      B.off_za = off + vb;
+      B.off_zb = off + 2 * vb;
+      B.off_t = off + 3 * vb;
+      off += 4 * vb;
+    }
+    return off;
+  };
+  int smem = layout(16);
+  const int cs = lowp ? bottom_cluster_size<float, float>(smem) : bottom_cluster_size<double, double>(smem);
+  if (cs != 16) smem = layout(cs);
   for (int j = 0; j < a.nb; ++j) {
     Level& L = h->L[kb + j];
     const bool coarsest = kb + j == h->nl - 1;
-    BotLevel& B = a.L[j];
-    B.n = L.n;
-    B.rp = L.rp;
-    B.ci = L.ci;
-    B.v = L.lowp ? (const void*)L.vf : (const void*)L.v;
-    B.dinv = L.lowp ? (const void*)L.dinvf : (const void*)L.dinv;
-    B.agg = coarsest ? nullptr : L.agg;
-    B.mptr = coarsest ? nullptr : L.mptr;
-    B.mem = coarsest ? nullptr : L.mem;
-    B.r = L.r;
-    B.za = L.za;
-    B.zb = L.zb;
-    B.t = L.t;
     const double n = L.n, sx = vec_bytes(L), sv = val_bytes(L);
     if (coarsest) {
       bytes += 3.0 * sx * n + (h->p.coarse_sweeps - 1) * (row_pass(L, sv) + 4.0 * sx * n);
@@ -624,8 +646,8 @@ static void rec_bottom(VRec& R) {
       bytes += 4.0 * n + sc * nc + 2.0 * sx * n;                         // prolongation
     }
   }
-  if (h->L[kb].lowp) launch_bottom<float, float>(R.s, a);
-  else launch_bottom<double, double>(R.s, a);
+  if (lowp) launch_bottom<float, float>(R.s, a, cs, smem);
+  else launch_bottom<double, double>(R.s, a, cs, smem);
   R.add(bytes);
 }
 
