@@ -331,8 +331,8 @@ def main():
     t_vc = g.time_vcycle(reps=20)
     vc_gbs = info["vcycle_bytes"] / (t_vc * 1e-3) / 1e9
     kernels = {}
-    names = {amg.K_SWEEP: "sweep", amg.K_RESIDUAL: "residual", amg.K_RESTRICT: "restrict",
-             amg.K_PROLONG: "prolong", amg.K_SPMV_DOTS: "spmv_dots", amg.K_AXPY: "axpy"}
+    names = {amg.K_SWEEP: "sweep", amg.K_RESIDUAL: "residual", amg.K_RESTRICT_FIRST: "restrict_first_sweep",
+             amg.K_SWEEP_PROLONG: "coarse_sweep_prolong", amg.K_SPMV_DOTS: "spmv_dots", amg.K_AXPY: "axpy"}
     for kid, nm in names.items():
         t = g.time_kernel(kid, 0, reps=30)
         by = g.kernel_bytes(kid, 0)

@@ -151,7 +151,10 @@ amg_status amg_get_l1(amg_handle* h, int32_t level, double* l1_host);
  * amg_time_kernel: average duration of one launch of kernel `which` on `level`
  *   over reps launches, timed with CUDA events on the handle's stream:
  *   0 = l1-Jacobi sweep, 1 = residual, 2 = restriction, 3 = prolongation,
- *   4 = outer SpMV fused with the dot products, 5 = fused axpys.
+ *   4 = outer SpMV fused with the dot products, 5 = fused axpys,
+ *   6 = restriction from `level` fused with the first sweep of level+1,
+ *   7 = l1-Jacobi sweep of level+1 fused with the prolongation into `level`
+ *   (6 and 7 are the forms the V-cycle launches; 2 and 3 the unfused ones).
  */
 amg_status amg_time_vcycle(amg_handle* h, int32_t reps, double* ms);
 amg_status amg_time_kernel(amg_handle* h, int32_t which, int32_t level, int32_t reps, double* ms);

@@ -112,6 +112,7 @@ struct amg_handle {
   int use_bottom = 0;          // 1: bottom levels in one cluster launch (measured slower; off)
   int small_rows = 0;          // levels with fewer rows use the non-pipelined tiled kernels
   int min_tpr = 1;             // tuning hook: least threads per row of the pipelined kernels
+  int fuse = 1;                // restriction and prolongation fused into the coarse level's first / last sweep
   int kb = AMG_MAXL;           // first level of the fused bottom (nl: none)
   long long suitor_cap = -1;   // test hook: step cap of the matching loop (-1: proof-level bound)
   int fail_alloc_after = -1;   // test hook: the allocation with this index fails (-1: never)

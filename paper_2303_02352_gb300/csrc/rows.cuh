@@ -90,7 +90,11 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
   }
 }
 
-enum { PM_SWEEP = 0, PM_RESID = 1, PM_SPMV = 2, PM_DOTS = 3, PM_RINIT = 4, PM_RTRUE = 5, PM_RNORM = 6 };
+// PM_SWEEP_PROLONG: an l1-Jacobi sweep of a coarse level whose result is also
+// added to the next finer level's iterate, z_f[i] += z_c[J] for every member i
+// of aggregate J (the unit piecewise-constant prolongation of the V-cycle)
+enum { PM_SWEEP = 0, PM_RESID = 1, PM_SPMV = 2, PM_DOTS = 3, PM_RINIT = 4, PM_RTRUE = 5, PM_RNORM = 6,
+       PM_SWEEP_PROLONG = 7 };
 
 template <typename MT, typename VT, typename OT>
 struct RowArgs {
@@ -109,7 +113,42 @@ struct RowArgs {
   double* partial;
   unsigned* counter;
   int* flags;
+  // PM_SWEEP_PROLONG: members of each row's aggregate and the finer iterate
+  const int32_t* mptr;
+  const int32_t* mem;
+  void* zf;
+  int zf64;  // the finer iterate is double (else float)
 };
+
+// z_f[i] += z for the members i of aggregate `row`, in the finer level's
+// vector type.  The TPR lanes of the row share the members (lane `sub` takes
+// members sub, sub + TPR, ...); each lane loads up to 8 member ids, then their
+// z_f entries, then stores, so one row costs three dependent round trips.
+template <typename FT, typename OT>
+__device__ __forceinline__ void prolong_chunk(FT* zf, const int32_t* mem, int base, int m1, int step, OT z) {
+  int idx[8];
+  FT v[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int m = base + u * step;
+    idx[u] = m < m1 ? __ldg(&mem[m]) : -1;
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+    if (idx[u] >= 0) v[u] = zf[idx[u]];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+    if (idx[u] >= 0) zf[idx[u]] = v[u] + (FT)z;
+}
+
+template <int TPR, typename MT, typename VT, typename OT>
+__device__ __forceinline__ void prolong_members(const RowArgs<MT, VT, OT>& a, int row, int sub, OT z) {
+  const int m1 = __ldg(&a.mptr[row + 1]);
+  for (int base = __ldg(&a.mptr[row]) + sub; base < m1; base += 8 * TPR) {
+    if (a.zf64) prolong_chunk(static_cast<double*>(a.zf), a.mem, base, m1, TPR, z);
+    else prolong_chunk(static_cast<float*>(a.zf), a.mem, base, m1, TPR, z);
+  }
+}
 
 __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
@@ -178,7 +217,7 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
 
   if (early) pdl_wait();  // the previous kernel's results (vectors, flags) are visible from here on
   bool skip = false;
-  if constexpr (MODE == PM_SWEEP || MODE == PM_RESID) skip = *a.skip != 0;
+  if constexpr (MODE == PM_SWEEP || MODE == PM_RESID || MODE == PM_SWEEP_PROLONG) skip = *a.skip != 0;
   else if constexpr (MODE == PM_DOTS) skip = a.st->done != 0;
   else if constexpr (MODE == PM_RTRUE) skip = a.st->done || !a.st->need_true;
   if (skip) {
@@ -230,12 +269,13 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
       const int p0 = __ldg(&a.rp[row0]);
       int q0 = 0, q1 = 0;
       VT own = 0, rr = 0, dd = 0, qq = 0;
+      OT zn = 0;  // PM_SWEEP_PROLONG: the row's new value
       if (live) {
         q0 = __ldg(&a.rp[row]) + sub;
         q1 = __ldg(&a.rp[row + 1]);
       }
       if (lead) {
-        if constexpr (MODE == PM_SWEEP) {
+        if constexpr (MODE == PM_SWEEP || MODE == PM_SWEEP_PROLONG) {
           own = __ldg(&a.x[row]);
           rr = __ldg(&a.r[row]);
           dd = __ldg(&a.dinv[row]);
@@ -264,6 +304,9 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
       if (lead) {
         if constexpr (MODE == PM_SWEEP) {
           a.out[row] = (OT)(own + dd * (rr - s));
+        } else if constexpr (MODE == PM_SWEEP_PROLONG) {
+          zn = (OT)(own + dd * (rr - s));
+          a.out[row] = zn;
         } else if constexpr (MODE == PM_RESID) {
           a.out[row] = (OT)(rr - s);
         } else if constexpr (MODE == PM_SPMV) {
@@ -279,6 +322,10 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
           acc[0] += ri * ri;
           if constexpr (MODE == PM_RINIT) acc[1] += (double)rr * (double)rr;
         }
+      }
+      if constexpr (MODE == PM_SWEEP_PROLONG) {
+        if constexpr (TPR > 1) zn = __shfl_sync(0xffffffffu, zn, 0, TPR);  // from the row's lead lane
+        if (live) prolong_members<TPR>(a, row, sub, zn);
       }
     }
   }

@@ -842,6 +842,7 @@ extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* str
   if (const char* e = getenv("AMG_BOTTOM")) h->use_bottom = atoi(e);
   if (const char* e = getenv("AMG_SMALL_ROWS")) h->small_rows = atoi(e);
   if (const char* e = getenv("AMG_MIN_TPR")) h->min_tpr = atoi(e);
+  if (const char* e = getenv("AMG_FUSE")) h->fuse = atoi(e);
   if (const char* e = getenv("AMG_FAIL_ALLOC_AFTER")) h->fail_alloc_after = atoi(e);
   if (const char* e = getenv("AMG_PIPE")) h->use_pipe = atoi(e);
   if (const char* e = getenv("AMG_STAGES")) h->stages = atoi(e);

@@ -166,6 +166,26 @@ __global__ void __launch_bounds__(AMG_BLOCK) k_restrict(int nc, const int32_t* _
   rc[J] = (CT)s;
 }
 
+// restriction fused with the coarse level's first sweep from zero:
+// r_c[J] = sum over the members i of J (ascending) of t_i, z_c[J] = D_c[J] r_c[J]
+// (the same roundings as the restriction followed by the first sweep)
+template <typename VT, typename CT>
+__global__ void __launch_bounds__(AMG_BLOCK) k_restrict_first(int nc, const int32_t* __restrict__ mptr,
+                                                              const int32_t* __restrict__ mem, const VT* __restrict__ t,
+                                                              const CT* __restrict__ dinv_c, CT* __restrict__ rc,
+                                                              CT* __restrict__ zc, const int* skip) {
+  pdl_trigger();
+  pdl_wait();
+  if (*skip) return;
+  const int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= nc) return;
+  VT s = 0;
+  for (int m = mptr[J]; m < mptr[J + 1]; ++m) s += t[mem[m]];
+  const CT r = (CT)s;
+  rc[J] = r;
+  zc[J] = dinv_c[J] * r;
+}
+
 // z_i += z_c[agg(i)]  (unit piecewise-constant prolongator)
 template <typename VT, typename CT>
 __global__ void __launch_bounds__(AMG_BLOCK) k_prolong(int n, const int32_t* __restrict__ agg, const CT* __restrict__ zc,
@@ -486,6 +506,31 @@ static void launch_sweep(cudaStream_t s, const Level& L, const MT* vals, const V
   DISPATCH_R(R, (amg_launch(k_sweep<TR, MT, VT, OT>, dim3(nb), dim3(TR), 0, s, L.n, L.rp, L.ci, vals, dinv, r, z, out, skip)));
 }
 
+// grid of the pipelined row kernel of `MODE` on a level with tiles of R rows
+template <int MODE, typename MT, typename VT, typename OT>
+static int rows_grid(int R, int n) {
+  int g = 0;
+  DISPATCH_TPR(PIPE_CONSUMERS / R, (g = pipe_grid<TP, 2, MODE, MT, VT, OT>(n)));
+  return g;
+}
+
+// sweep of a coarse level fused with the prolongation of its result into the
+// finer level's iterate zf.  Only where every block of the sweep has at most
+// one tile (a latency-bound level: the fused kernel saves a launch); on larger
+// levels the member scatter inside the tile loop costs more than the separate
+// prolongation kernel (measured).  false: nothing launched.
+template <typename MT, typename VT>
+static bool launch_sweep_prolong(cudaStream_t s, const Level& C, const MT* vals, const VT* dinv, const VT* r, const VT* z,
+                                 VT* out, const int* skip, int* flags, const Level& F, void* zf, bool any_size = false) {
+  if (!C.pipe) return false;
+  const int tiles = (C.n + C.R - 1) / C.R;
+  if (!any_size && rows_grid<PM_SWEEP_PROLONG, MT, VT, VT>(C.R, C.n) < tiles) return false;
+  RowArgs<MT, VT, VT> a{C.n, C.rp, C.ci, vals, z, dinv, r, nullptr, nullptr, out, skip, nullptr, nullptr, nullptr, flags,
+                        F.mptr, F.mem, zf, F.lowp ? 0 : 1};
+  launch_rows<PM_SWEEP_PROLONG>(s, C.R, 2, a);
+  return true;
+}
+
 template <typename MT, typename VT>
 static void launch_resid(cudaStream_t s, const Level& L, const MT* vals, const VT* r, const VT* z, VT* t, const int* skip,
                          int* flags, int stages) {
@@ -552,9 +597,26 @@ static double row_pass(const Level& L, double sv) { return (double)L.nnz * (sv +
 static double val_bytes(const Level& L) { return L.lowp ? (L.vb ? 2.0 : 4.0) : 8.0; }
 static double vec_bytes(const Level& L) { return L.lowp ? 4.0 : 8.0; }
 
+// prolongation target handed to a coarse level: the finer level and its
+// iterate.  The coarse level's last sweep adds its result to that iterate
+// (PM_SWEEP_PROLONG) and sets `done`; otherwise the caller prolongs.
+struct Prol {
+  const Level* F;
+  void* z;
+  bool done;
+};
+
+// extra algorithmic bytes of a sweep that also prolongs: the aggregates'
+// member pointers and ids, read-modify-write of the finer iterate
+static double prolong_fused_bytes(const Level& F, const Level& C) {
+  return 4.0 * (C.n + 1.0) + 4.0 * F.n + 2.0 * vec_bytes(F) * F.n;
+}
+
 // coarsest level: `sweeps` l1-Jacobi sweeps from zero on r (double); returns the
-// buffer that holds the result
-static double* rec_coarse(VRec& R, int k, const double* r, double* final_out) {
+// buffer that holds the result.  first_done: the restriction already wrote the
+// first sweep's result D r into za.
+static double* rec_coarse(VRec& R, int k, const double* r, double* final_out, bool first_done = false,
+                          Prol* pro = nullptr) {
   Level& L = R.h->L[k];
   double* za = (double*)L.za;
   double* zb = (double*)L.zb;
@@ -567,14 +629,23 @@ static double* rec_coarse(VRec& R, int k, const double* r, double* final_out) {
     R.add(8.0 * n);
     return o;
   }
-  double* o = (sweeps == 1 && final_out) ? final_out : za;
-  amg_launch(k_first<double, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.dinv, r, nullptr, o, R.skip);
-  R.add(24.0 * n);
+  double* o = za;
+  if (!first_done) {
+    if (sweeps == 1 && final_out) o = final_out;
+    amg_launch(k_first<double, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.dinv, r, nullptr, o, R.skip);
+    R.add(24.0 * n);
+  }
   cur = o;
   for (int sw = 1; sw < sweeps; ++sw) {
     double* nxt = (sw == sweeps - 1 && final_out) ? final_out : (cur == za ? zb : za);
-    launch_sweep<double, double, double>(R.s, L, L.v, L.dinv, r, cur, nxt, R.skip, R.h->dev_flags, R.h->stages);
-    R.add(row_pass(L, 8.0) + 32.0 * n);
+    if (sw == sweeps - 1 && pro &&
+        launch_sweep_prolong<double, double>(R.s, L, L.v, L.dinv, r, cur, nxt, R.skip, R.h->dev_flags, *pro->F, pro->z)) {
+      pro->done = true;
+      R.add(row_pass(L, 8.0) + 32.0 * n + prolong_fused_bytes(*pro->F, L));
+    } else {
+      launch_sweep<double, double, double>(R.s, L, L.v, L.dinv, r, cur, nxt, R.skip, R.h->dev_flags, R.h->stages);
+      R.add(row_pass(L, 8.0) + 32.0 * n);
+    }
     cur = nxt;
   }
   return cur;
@@ -582,8 +653,10 @@ static double* rec_coarse(VRec& R, int k, const double* r, double* final_out) {
 
 // level k in type VT with matrix values MT.  rin: level input (RT = double at
 // level 0, VT elsewhere).  final_out (level 0 only): where the last sweep writes.
+// first_done: the restriction already wrote the first sweep's result into za.
+// pro: where the last post-smoothing sweep prolongs its result (if it can).
 template <typename VT, typename MT, typename RT>
-static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out);
+static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out, bool first_done = false, Prol* pro = nullptr);
 
 // the bottom levels kb .. nl-1 in one cluster launch; result in L[kb].za
 static void rec_bottom(VRec& R) {
@@ -675,10 +748,21 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
     return;
   }
   const bool wcyc = h->p.cycle == 2;
+  // restriction fused with the coarse level's first sweep, prolongation with
+  // its last sweep (not in the W-cycle, whose correction sums two visits)
+  const bool fuse = h->fuse && !wcyc;
+  Prol pro{&L, (void*)z, false};
   if (k + 1 == h->nl - 1) {  // coarsest: FP64
-    amg_launch(k_restrict<VT, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (double*)C.r, R.skip);
-    R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 8.0 * nc);
-    double* zc = rec_coarse(R, k + 1, (const double*)C.r, nullptr);
+    const bool fr = fuse && h->p.coarse_sweeps > 0;
+    if (fr) {
+      amg_launch(k_restrict_first<VT, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t,
+                 (const double*)C.dinv, (double*)C.r, (double*)C.za, R.skip);
+      R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 24.0 * nc);
+    } else {
+      amg_launch(k_restrict<VT, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (double*)C.r, R.skip);
+      R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 8.0 * nc);
+    }
+    double* zc = rec_coarse(R, k + 1, (const double*)C.r, nullptr, fr, fuse ? &pro : nullptr);
     if (wcyc) {  // W-cycle: e = z_c;  r2 = r_c - A_c e;  e += B_c r2
       double* e = (double*)C.e;
       double* r2 = (double*)C.r2;
@@ -691,15 +775,26 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
       R.add(24.0 * nc);
       zc = e;
     }
-    amg_launch(k_prolong<VT, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip);
-    R.add(4.0 * n + 8.0 * nc + 2.0 * sx * n);
+    if (!pro.done) {
+      amg_launch(k_prolong<VT, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip);
+      R.add(4.0 * n + 8.0 * nc + 2.0 * sx * n);
+    }
   } else {
     const double sc = vec_bytes(C);
-    amg_launch(k_restrict<VT, VT>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip);
-    R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc);
+    const bool fr = fuse && h->p.pre_sweeps > 0;
+    if (fr) {
+      const VT* dc = C.lowp ? (const VT*)C.dinvf : (const VT*)C.dinv;
+      amg_launch(k_restrict_first<VT, VT>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, dc,
+                 (VT*)C.r, (VT*)C.za, R.skip);
+      R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 3.0 * sc * nc);
+    } else {
+      amg_launch(k_restrict<VT, VT>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip);
+      R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc);
+    }
+    Prol* pp = fuse ? &pro : nullptr;
     VT* zc;
-    if (C.lowp) zc = (VT*)rec_level<float, float, float>(R, k + 1, (const float*)C.r, nullptr);
-    else zc = (VT*)rec_level<double, double, double>(R, k + 1, (const double*)C.r, nullptr);
+    if (C.lowp) zc = (VT*)rec_level<float, float, float>(R, k + 1, (const float*)C.r, nullptr, fr, pp);
+    else zc = (VT*)rec_level<double, double, double>(R, k + 1, (const double*)C.r, nullptr, fr, pp);
     if (wcyc) {
       VT* e = (VT*)C.e;
       VT* r2 = (VT*)C.r2;
@@ -717,13 +812,15 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
       R.add(3.0 * sc * nc);
       zc = e;
     }
-    amg_launch(k_prolong<VT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip);
-    R.add(4.0 * n + sc * nc + 2.0 * sx * n);
+    if (!pro.done) {
+      amg_launch(k_prolong<VT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip);
+      R.add(4.0 * n + sc * nc + 2.0 * sx * n);
+    }
   }
 }
 
 template <typename VT, typename MT, typename RT>
-static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out) {
+static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out, bool first_done, Prol* pro) {
   amg_handle* h = R.h;
   Level& L = h->L[k];
   const MT* vals;
@@ -751,8 +848,10 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out) {
   // pre-smoothing from zero
   VT* cur = za;
   if (h->p.pre_sweeps > 0) {
-    amg_launch(k_first<RT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, dinv, rin, rcopy, za, R.skip);
-    R.add(sr * n + 2.0 * sx * n + rc_bytes);
+    if (!first_done) {
+      amg_launch(k_first<RT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, dinv, rin, rcopy, za, R.skip);
+      R.add(sr * n + 2.0 * sx * n + rc_bytes);
+    }
     for (int sw = 1; sw < h->p.pre_sweeps; ++sw) {
       VT* nxt = cur == za ? zb : za;
       launch_sweep<MT, VT, VT>(R.s, L, vals, dinv, r, cur, nxt, R.skip, h->dev_flags, h->stages);
@@ -785,8 +884,14 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out) {
       R.add(row_pass(L, sv) + 3.0 * sx * n + 8.0 * n);
       return nullptr;
     }
-    launch_sweep<MT, VT, VT>(R.s, L, vals, dinv, r, cur, nxt, R.skip, h->dev_flags, h->stages);
-    R.add(row_pass(L, sv) + 4.0 * sx * n);
+    if (sw == post - 1 && pro &&
+        launch_sweep_prolong<MT, VT>(R.s, L, vals, dinv, r, cur, nxt, R.skip, h->dev_flags, *pro->F, pro->z)) {
+      pro->done = true;
+      R.add(row_pass(L, sv) + 4.0 * sx * n + prolong_fused_bytes(*pro->F, L));
+    } else {
+      launch_sweep<MT, VT, VT>(R.s, L, vals, dinv, r, cur, nxt, R.skip, h->dev_flags, h->stages);
+      R.add(row_pass(L, sv) + 4.0 * sx * n);
+    }
     cur = nxt;
   }
   return cur;
@@ -849,6 +954,15 @@ extern "C" amg_status amg_kernel_bytes(const amg_handle* h, int32_t which, int32
       const Level& C = h->L[level + 1];
       const double nc = C.n, sc = vec_bytes(C);
       *bytes = which == 2 ? 4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc : 4.0 * n + sc * nc + 2.0 * sx * n;
+      return AMG_OK;
+    }
+    case 6:
+    case 7: {
+      if (last) return AMG_ERR_INVALID_ARG;
+      const Level& C = h->L[level + 1];
+      const double nc = C.n, sc = vec_bytes(C);
+      *bytes = which == 6 ? 4.0 * (nc + 1) + 4.0 * n + sx * n + 3.0 * sc * nc
+                          : row_pass(C, val_bytes(C)) + 4.0 * sc * nc + prolong_fused_bytes(L, C);
       return AMG_OK;
     }
     case 4: *bytes = level == 0 ? bytes_spmv_dots(L) : 0.0; return level == 0 ? AMG_OK : AMG_ERR_INVALID_ARG;
@@ -1172,6 +1286,36 @@ static amg_status launch_one(amg_handle* h, int which, int k) {
         if (!L.lowp) amg_launch(k_prolong<double, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (double*)C.za, (double*)L.za, skip);
         else if (ccoarse) amg_launch(k_prolong<float, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (double*)C.za, (float*)L.za, skip);
         else amg_launch(k_prolong<float, float>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (float*)C.za, (float*)L.za, skip);
+      }
+      break;
+    }
+    case 6:
+    case 7: {
+      if (coarsest) return amg_fail(h, AMG_ERR_INVALID_ARG, "no restriction/prolongation on the coarsest level");
+      Level& C = h->L[k + 1];
+      const bool ccoarse = (k + 1 == h->nl - 1);
+      if (which == 6) {
+        if (ccoarse && !L.lowp)
+          amg_launch(k_restrict_first<double, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem,
+                     (const double*)L.t, (const double*)C.dinv, (double*)C.r, (double*)C.za, skip);
+        else if (ccoarse)
+          amg_launch(k_restrict_first<float, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem,
+                     (const float*)L.t, (const double*)C.dinv, (double*)C.r, (double*)C.za, skip);
+        else if (!L.lowp)
+          amg_launch(k_restrict_first<double, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem,
+                     (const double*)L.t, (const double*)C.dinv, (double*)C.r, (double*)C.za, skip);
+        else
+          amg_launch(k_restrict_first<float, float>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem,
+                     (const float*)L.t, (const float*)C.dinvf, (float*)C.r, (float*)C.za, skip);
+      } else {
+        bool ok;
+        if (ccoarse || !C.lowp)
+          ok = launch_sweep_prolong<double, double>(s, C, C.v, C.dinv, (const double*)C.r, (const double*)C.za,
+                                                    (double*)C.zb, skip, h->dev_flags, L, L.za, true);
+        else
+          ok = launch_sweep_prolong<float, float>(s, C, C.vf, C.dinvf, (const float*)C.r, (const float*)C.za,
+                                                  (float*)C.zb, skip, h->dev_flags, L, L.za, true);
+        if (!ok) return amg_fail(h, AMG_ERR_INVALID_ARG, "level %d runs the non-pipelined kernels", k + 1);
       }
       break;
     }

@@ -318,6 +318,54 @@ def test_fused_bottom_matches_separate_launches(name, prec, monkeypatch):
         assert gg.pcg_solve(b)["true_rel_res"] < 1e-6
 
 
+@pytest.mark.parametrize("name", ["poisson13", "poisson32", "diff27_12", "laplace1d"])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_fused_restrict_prolong_bitwise(name, prec, monkeypatch):
+    """Restriction fused with the coarse first sweep and prolongation fused with
+    the coarse last sweep round exactly like the separate kernels."""
+    A = PROBLEMS[name]()
+    r = W.random_vector(A.n, 21)
+    monkeypatch.setenv("AMG_FUSE", "0")
+    z0 = G(A, precision=prec).vcycle(r).cpu().numpy()
+    monkeypatch.setenv("AMG_FUSE", "1")
+    g = G(A, precision=prec)
+    z1 = g.vcycle(r).cpu().numpy()
+    assert np.array_equal(z0, z1)
+    # fused forms on the non-pipelined kernels fall back to separate launches
+    monkeypatch.setenv("AMG_SMALL_ROWS", "100000000")
+    z2 = G(A, precision=prec).vcycle(r).cpu().numpy()
+    assert rel(z2, z0) < (1e-13 if prec == 0 else 1e-6)
+    if prec == 0:
+        assert rel(z1, O.Hierarchy(A).vcycle(r)) < 1e-12
+
+
+@pytest.mark.parametrize("kw", [dict(pre_sweeps=0), dict(post_sweeps=0), dict(coarse_sweeps=1),
+                                dict(coarse_sweeps=2, pre_sweeps=1, post_sweeps=1),
+                                dict(pre_sweeps=0, post_sweeps=0, coarse_sweeps=0)])
+def test_fused_forms_with_edge_sweep_counts(kw):
+    """Sweep counts at which a fused form does not apply (no first or no last
+    sweep on the coarse level) against the oracle."""
+    A = W.diffusion7(15, 1.5, 5)
+    r = W.random_vector(A.n, 4)
+    kw = dict(kw, coarse_size=30)
+    g, o = G(A, **kw), O.Hierarchy(A, **kw)
+    assert g.num_levels == o.num_levels >= 3
+    assert rel(g.vcycle(r).cpu().numpy(), o.vcycle(r)) < 1e-12
+
+
+def test_fused_kernel_timing_entries():
+    from paper_2303_02352_gb300 import amg
+    A = W.poisson7(24)
+    for prec in (0, 1):
+        g = G(A, precision=prec)
+        for kid in (amg.K_RESTRICT_FIRST, amg.K_SWEEP_PROLONG, amg.K_RESTRICT, amg.K_PROLONG):
+            assert g.time_kernel(kid, 0, reps=3) > 0.0
+            assert g.kernel_bytes(kid, 0) > 0.0
+        # no restriction below the coarsest level
+        with pytest.raises(RuntimeError):
+            g.time_kernel(amg.K_RESTRICT_FIRST, g.num_levels - 1, reps=1)
+
+
 @pytest.mark.parametrize("np_", [2, 5])
 def test_decoupled_aggregation_parity(np_):
     A = W.diffusion27(12, 2.0, 21)
