@@ -83,6 +83,7 @@ struct Level {
 };
 
 struct AdjState;  // adjoint work buffers (learned.cu)
+struct BotPlan;   // fused-bottom launch arguments (solve.cu)
 
 struct amg_handle {
   amg_params p{};
@@ -109,11 +110,12 @@ struct amg_handle {
   int ax_grid = 0;             // grid of the fused axpys
   int stages = 2;              // pipeline depth of the row kernels (2 measured best: more stages cost resident blocks)
   int use_pipe = 1;            // 0: non-pipelined tiled row kernels
-  int use_bottom = 0;          // 1: bottom levels in one cluster launch (measured slower; off)
+  int use_bottom = 2;          // bottom levels in one cluster launch: 0 never, 1 always (if they fit), 2 where the owner spread says it pays
   int small_rows = 0;          // levels with fewer rows use the non-pipelined tiled kernels
   int min_tpr = 1;             // tuning hook: least threads per row of the pipelined kernels
   int fuse = 1;                // restriction and prolongation fused into the coarse level's first / last sweep
   int kb = AMG_MAXL;           // first level of the fused bottom (nl: none)
+  BotPlan* bot = nullptr;      // launch arguments of the fused bottom (solve.cu)
   long long suitor_cap = -1;   // test hook: step cap of the matching loop (-1: proof-level bound)
   int fail_alloc_after = -1;   // test hook: the allocation with this index fails (-1: never)
   int n_allocs = 0;
@@ -183,6 +185,8 @@ int amg_num_sms();  // multiprocessors of the current device
 
 // solve-phase internals (solve.cu)
 amg_status amg_prepare_solve(amg_handle* h);
+amg_status amg_plan_bottom(amg_handle* h);        // chooses kb and lays out the fused bottom (solve.cu)
+void amg_free_bottom(amg_handle* h);
 amg_status amg_capture_graphs(amg_handle* h);
 
 // ---------------------------------------------------------------------------

@@ -90,6 +90,7 @@ extern "C" void amg_destroy(amg_handle* h) {
   cudaStreamSynchronize(h->stream);
   amg_release_graphs(h);
   amg_adj_destroy(h);
+  amg_free_bottom(h);
   amg_free_all(h);
   delete h;
 }

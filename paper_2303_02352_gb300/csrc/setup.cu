@@ -809,18 +809,15 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
       if (st != AMG_OK) return st;
     }
   }
-  // fused bottom: the levels k >= 1 with at most 16384 rows (at most 8 of them)
   h->kb = h->nl;
   if (h->p.cycle != 0 && h->p.cycle != 2)
     return amg_fail(h, AMG_ERR_INVALID_ARG, "cycle must be 0 (V) or 2 (W)");
-  if (h->use_bottom && h->p.cycle == 0)
-    for (int k = 1; k < h->nl; ++k)
-      if (h->L[k].n <= 16384 && h->nl - k <= 8) {
-        h->kb = k;
-        break;
-      }
   AMG_CK(h, cudaStreamSynchronize(s));
   AMG_CK(h, cudaGetLastError());
+  if (h->use_bottom && h->p.cycle == 0) {  // the small levels in one cluster launch
+    amg_status st = amg_plan_bottom(h);
+    if (st != AMG_OK) return st;
+  }
   return amg_prepare_solve(h);
 }
 
@@ -835,7 +832,10 @@ extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* str
   else amg_params_default(&h->p);
   h->stream = (cudaStream_t)stream;
   // test and tuning hooks (environment): AMG_PIPE=0 non-pipelined row kernels,
-  // AMG_STAGES pipeline depth, AMG_BOTTOM=0 bottom levels as separate launches,
+  // AMG_STAGES pipeline depth, AMG_BOTTOM=0/1/2 bottom levels as separate
+  // launches / in one cluster launch / by the owner-spread rule (default),
+  // AMG_FUSE=0 restriction and prolongation as separate kernels,
+  // AMG_SMALL_ROWS, AMG_MIN_TPR row-kernel forms,
   // AMG_SUITOR_CAP step cap of the matching loop,
   // AMG_FAIL_ALLOC_AFTER make the k-th device allocation of the handle fail
   if (const char* e = getenv("AMG_SUITOR_CAP")) h->suitor_cap = atoll(e);

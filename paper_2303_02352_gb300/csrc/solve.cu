@@ -658,69 +658,188 @@ static double* rec_coarse(VRec& R, int k, const double* r, double* final_out, bo
 template <typename VT, typename MT, typename RT>
 static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out, bool first_done = false, Prol* pro = nullptr);
 
+// ---------------------------------------------------------------------------
+// fused bottom: plan (at setup) and recording
+
+struct BotPlan {
+  BotArgs a;
+  int cs = 0;      // cluster size
+  int smem = 0;    // dynamic shared memory per block
+  double bytes = 0.0;
+};
+
+void amg_free_bottom(amg_handle* h) {
+  delete h->bot;
+  h->bot = nullptr;
+}
+
+static int align16(int x) { return (x + 15) & ~15; }
+
+// layout of the bottom levels kb .. nl-1 for a cluster of cs blocks; returns
+// the shared memory per block.  rps[j] / mps[j]: host copies of level kb+j's
+// row pointers and member pointers.
+static long long bottom_layout(amg_handle* h, int kb, int cs, BotArgs& a, const std::vector<std::vector<int32_t>>& rps,
+                               const std::vector<std::vector<int32_t>>& mps) {
+  a.nb = h->nl - kb;
+  long long off = 0;
+  for (int j = 0; j < a.nb; ++j) {
+    const Level& L = h->L[kb + j];
+    const bool coarsest = kb + j == h->nl - 1;
+    BotLevel& B = a.L[j];
+    const int es = coarsest ? 8 : (L.lowp ? 4 : 8);  // vector and value bytes
+    const int chunk = (L.n + cs - 1) / cs;
+    B.n = L.n;
+    B.chunk = chunk;
+    B.magic = ((1ull << 32) + (unsigned long long)chunk - 1) / (unsigned long long)chunk;
+    B.rp = L.rp;
+    B.ci = L.ci;
+    B.v = (!coarsest && L.lowp) ? (const void*)L.vf : (const void*)L.v;
+    B.dinv = (!coarsest && L.lowp) ? (const void*)L.dinvf : (const void*)L.dinv;
+    int emax = 0;
+    for (int c = 0; c <= BOT_MAX_CS; ++c) B.e0[c] = rps[j][std::min(c * chunk, L.n)];
+    for (int c = 0; c < cs; ++c) emax = std::max(emax, B.e0[c + 1] - B.e0[c]);
+    int cchunk = 0, mmax = 0;
+    if (!coarsest) {
+      const Level& C = h->L[kb + j + 1];
+      cchunk = (C.n + cs - 1) / cs;
+      for (int c = 0; c <= BOT_MAX_CS; ++c) B.m0[c] = mps[j][std::min(c * cchunk, C.n)];
+      for (int c = 0; c < cs; ++c) mmax = std::max(mmax, B.m0[c + 1] - B.m0[c]);
+      B.agg = L.agg;
+      B.mptr = L.mptr;
+      B.mem = L.mem;
+    } else {
+      B.agg = B.mptr = B.mem = nullptr;
+      for (int c = 0; c <= BOT_MAX_CS; ++c) B.m0[c] = 0;
+    }
+    auto take = [&](long long bytes) {
+      const int o = (int)off;
+      off += align16((int)bytes);
+      return o;
+    };
+    B.o_rp = take(4ll * (chunk + 1));
+    B.o_ci = take(4ll * emax);
+    B.o_v = take((long long)es * emax);
+    B.o_dinv = take((long long)es * chunk);
+    B.o_agg = coarsest ? 0 : take(4ll * chunk);
+    B.o_mptr = coarsest ? 0 : take(4ll * (cchunk + 1));
+    B.o_mem = coarsest ? 0 : take(4ll * mmax);
+    B.o_r = take((long long)es * chunk);
+    B.o_za = take((long long)es * chunk);
+    B.o_zb = take((long long)es * chunk);
+    B.o_t = take((long long)es * chunk);
+  }
+  return off;
+}
+
+// mean number of distinct owner blocks that one warp-wide load of the row
+// kernel reaches: warps take 32 consecutive rows of a block, load u takes the
+// u-th entry of each row.  Loads that reach several blocks are served one
+// block after another, so the fused bottom pays off only where this stays
+// near 1 (regular stencil hierarchies: 1.1-1.3; irregular 27-point coarse
+// levels: 1.9-2.5).
+static double owner_spread(const std::vector<int32_t>& rp, const std::vector<int32_t>& ci, int n, int chunk) {
+  double tot = 0.0, cnt = 0.0;
+  for (int r0 = 0; r0 < n; r0 += chunk) {
+    const int r1 = std::min(n, r0 + chunk);
+    for (int w0 = r0; w0 < r1; w0 += 32) {
+      const int w1 = std::min(r1, w0 + 32);
+      int len = 0;
+      for (int i = w0; i < w1; ++i) len = std::max(len, rp[i + 1] - rp[i]);
+      for (int u = 0; u < len; ++u) {
+        int owners[32], no = 0;
+        for (int i = w0; i < w1; ++i) {
+          if (rp[i] + u >= rp[i + 1]) continue;
+          const int o = ci[rp[i] + u] / chunk;
+          bool seen = false;
+          for (int q = 0; q < no; ++q) seen = seen || owners[q] == o;
+          if (!seen) owners[no++] = o;
+        }
+        tot += no;
+        cnt += 1.0;
+      }
+    }
+  }
+  return cnt > 0.0 ? tot / cnt : 1.0;
+}
+
+// the first level kb >= 1 from which every level has at most BOT_MAX_ROWS rows
+// and whose slices fit one cluster's shared memory (16 blocks, else 8).  In
+// the automatic mode (use_bottom = 2) the plan is kept only where every
+// bottom level's owner spread is at most 1.5.
+amg_status amg_plan_bottom(amg_handle* h) {
+  amg_free_bottom(h);
+  h->kb = h->nl;
+  int k0 = 1;
+  while (k0 < h->nl && (h->L[k0].n > BOT_MAX_ROWS || h->nl - k0 > BOT_MAXL)) ++k0;
+  if (k0 >= h->nl) return AMG_OK;
+  std::vector<std::vector<int32_t>> rps(h->nl - k0), mps(h->nl - k0);
+  for (int k = k0; k < h->nl; ++k) {
+    const Level& L = h->L[k];
+    rps[k - k0].resize(L.n + 1);
+    AMG_CK(h, cudaMemcpy(rps[k - k0].data(), L.rp, 4ull * (L.n + 1), cudaMemcpyDeviceToHost));
+    if (k < h->nl - 1) {
+      const int nc = h->L[k + 1].n;
+      mps[k - k0].resize(nc + 1);
+      AMG_CK(h, cudaMemcpy(mps[k - k0].data(), L.mptr, 4ull * (nc + 1), cudaMemcpyDeviceToHost));
+    }
+  }
+  for (int kb = k0; kb < h->nl; ++kb) {
+    std::vector<std::vector<int32_t>> r(rps.begin() + (kb - k0), rps.end()), m(mps.begin() + (kb - k0), mps.end());
+    for (int cs : {16, 8}) {
+      BotPlan P;
+      const long long smem = bottom_layout(h, kb, cs, P.a, r, m);
+      if (smem > BOT_SMEM_MAX) continue;
+      const bool fits = h->L[kb].lowp ? bottom_fits<float>(cs, (int)smem) : bottom_fits<double>(cs, (int)smem);
+      if (!fits) continue;
+      if (h->use_bottom == 2) {
+        for (int k = kb; k < h->nl; ++k) {
+          const Level& L = h->L[k];
+          std::vector<int32_t> ci(L.nnz);
+          AMG_CK(h, cudaMemcpy(ci.data(), L.ci, 4ull * L.nnz, cudaMemcpyDeviceToHost));
+          if (owner_spread(rps[k - k0], ci, L.n, (L.n + cs - 1) / cs) > 1.5) return AMG_OK;
+        }
+      }
+      P.cs = cs;
+      P.smem = (int)smem;
+      h->bot = new BotPlan(P);
+      h->kb = kb;
+      return AMG_OK;
+    }
+  }
+  return AMG_OK;
+}
+
 // the bottom levels kb .. nl-1 in one cluster launch; result in L[kb].za
 static void rec_bottom(VRec& R) {
   amg_handle* h = R.h;
   const int kb = h->kb;
-  BotArgs a{};
-  a.nb = h->nl - kb;
+  BotPlan& P = *h->bot;
+  BotArgs a = P.a;
   a.pre = h->p.pre_sweeps;
   a.post = h->p.post_sweeps;
   a.csweeps = h->p.coarse_sweeps;
   a.skip = R.skip;
   a.r_in = h->L[kb].r;
   a.z_out = h->L[kb].za;
-  const bool lowp = h->L[kb].lowp;
-  double bytes = 0.0;
-  // layout for a cluster of cs blocks: chunk = next power of two >= ceil(n / cs)
-  auto layout = [&](int cs) {
-    int off = 0;
-    for (int j = 0; j < a.nb; ++j) {
-      Level& L = h->L[kb + j];
-      const bool coarsest = kb + j == h->nl - 1;
-      BotLevel& B = a.L[j];
-      const int per = (L.n + cs - 1) / cs;
-      int sh = 0;
-      while ((1 << sh) < per) ++sh;
-      const int es = coarsest ? 8 : (L.lowp ? 4 : 8);
-      const int vb = (((1 << sh) * es + 15) / 16) * 16;
-      B.n = L.n;
-      B.shift = sh;
-      B.rp = L.rp;
-      B.ci = L.ci;
-      B.v = L.lowp ? (const void*)L.vf : (const void*)L.v;
-      B.dinv = L.lowp ? (const void*)L.dinvf : (const void*)L.dinv;
-      B.agg = coarsest ? nullptr : L.agg;
-      B.mptr = coarsest ? nullptr : L.mptr;
-      B.mem = coarsest ? nullptr : L.mem;
-      B.off_r = off;
-      B.off_za = off + vb;
-      B.off_zb = off + 2 * vb;
-      B.off_t = off + 3 * vb;
-      off += 4 * vb;
-    }
-    return off;
-  };
-  int smem = layout(16);
-  const int cs = lowp ? bottom_cluster_size<float, float>(smem) : bottom_cluster_size<double, double>(smem);
-  if (cs != 16) smem = layout(cs);
+  double bytes = 0.0;  // the algorithmic bytes of the passes it replaces
   for (int j = 0; j < a.nb; ++j) {
     Level& L = h->L[kb + j];
     const bool coarsest = kb + j == h->nl - 1;
-    const double n = L.n, sx = vec_bytes(L), sv = val_bytes(L);
+    const double n = L.n, sx = coarsest ? 8.0 : vec_bytes(L), sv = coarsest ? 8.0 : val_bytes(L);
     if (coarsest) {
       bytes += 3.0 * sx * n + (h->p.coarse_sweeps - 1) * (row_pass(L, sv) + 4.0 * sx * n);
     } else {
       const Level& C = h->L[kb + j + 1];
-      const double nc = C.n, sc = vec_bytes(C);
+      const bool cc = kb + j + 1 == h->nl - 1;
+      const double nc = C.n, sc = cc ? 8.0 : vec_bytes(C);
       bytes += 3.0 * sx * n + (h->p.pre_sweeps - 1 + h->p.post_sweeps) * (row_pass(L, sv) + 4.0 * sx * n);
       bytes += row_pass(L, sv) + 3.0 * sx * n;                           // residual
       bytes += 4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc;              // restriction
       bytes += 4.0 * n + sc * nc + 2.0 * sx * n;                         // prolongation
     }
   }
-  if (lowp) launch_bottom<float, float>(R.s, a, cs, smem);
-  else launch_bottom<double, double>(R.s, a, cs, smem);
+  if (h->L[kb].lowp) launch_bottom<float>(R.s, a, P.cs, P.smem);
+  else launch_bottom<double>(R.s, a, P.cs, P.smem);
   R.add(bytes);
 }
 

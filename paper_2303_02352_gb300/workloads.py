@@ -11,7 +11,8 @@ with homogeneous Dirichlet conditions, discretised by finite differences):
   integer stencil (6, -1).  Scaling A and b by the same constant changes none of
   the iterates of the method, so the integer form keeps every value exact.
 * ``diffusion7(N, sigma, seed)``: 7-point stencil with a cellwise coefficient
-  k = exp(sigma * g), g a standard Gaussian that is constant on 8^3 blocks.  The
+  k = exp(sigma * g) rounded to float32, g a standard Gaussian that is
+  constant on 8^3 blocks.  The
   link coefficient between neighbouring cells is the harmonic mean
   2 k_i k_j / (k_i + k_j); a link that leaves the domain uses k_i.
 * ``diffusion27(N, sigma, seed)``: 27-point stencil with the same coefficient
@@ -99,10 +100,15 @@ def _offsets(points: int):
 
 
 def block_field(N: int, sigma: float, seed: int, block: int = 8) -> np.ndarray:
-    """Cellwise coefficient k = exp(sigma * g_B), g_B ~ N(0,1) per block^3 block."""
+    """Cellwise coefficient k = exp(sigma * g_B), g_B ~ N(0,1) per block^3 block.
+
+    The block values are rounded to float32 (and widened back): log, cos and exp
+    may differ in the last bit between math libraries, and the rounding makes
+    the matrix (and with it every tie of the matching) the same on every machine.
+    """
     nb = -(-N // block)
     g = gaussian(seed, np.arange(nb ** 3, dtype=np.uint64))
-    kb = np.exp(sigma * g)
+    kb = np.exp(sigma * g).astype(np.float32).astype(np.float64)
     c = np.arange(N) // block
     bz, by, bx = np.meshgrid(c, c, c, indexing="ij")
     return kb[(bx + nb * by + nb * nb * bz).ravel()]
