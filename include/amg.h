@@ -154,7 +154,10 @@ amg_status amg_get_l1(amg_handle* h, int32_t level, double* l1_host);
  *   4 = outer SpMV fused with the dot products, 5 = fused axpys,
  *   6 = restriction from `level` fused with the first sweep of level+1,
  *   7 = l1-Jacobi sweep of level+1 fused with the prolongation into `level`
- *   (6 and 7 are the forms the V-cycle launches; 2 and 3 the unfused ones).
+ *   (6 and 7 are the forms the V-cycle launches; 2 and 3 the unfused ones),
+ *   8 = two l1-Jacobi sweeps of `level` in one launch (the second pass reads
+ *   the matrix tiles the first pass brought into L2).
+ * amg_kernel_bytes of 8 counts the matrix once (the bytes that must move).
  */
 amg_status amg_time_vcycle(amg_handle* h, int32_t reps, double* ms);
 amg_status amg_time_kernel(amg_handle* h, int32_t which, int32_t level, int32_t reps, double* ms);

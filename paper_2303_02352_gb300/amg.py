@@ -17,7 +17,8 @@ SO_PATH = os.path.join(_HERE, "_build", "libamg.so")
 OK, NOT_CONVERGED = 0, 1
 ERR_INVALID_ARG, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_TOO_LARGE = -1, -2, -3, -4, -5, -6, -7
 FP64, FP32, FP32_BF16FINE = 0, 1, 2
-K_SWEEP, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_SPMV_DOTS, K_AXPY, K_RESTRICT_FIRST, K_SWEEP_PROLONG = range(8)
+(K_SWEEP, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_SPMV_DOTS, K_AXPY, K_RESTRICT_FIRST, K_SWEEP_PROLONG,
+ K_SWEEP_PAIR) = range(9)
 
 _STATUS = {0: "AMG_OK", 1: "AMG_NOT_CONVERGED", -1: "AMG_ERR_INVALID_ARG", -2: "AMG_ERR_NOT_SPD",
            -3: "AMG_ERR_BREAKDOWN", -4: "AMG_ERR_CUDA", -5: "AMG_ERR_OOM", -6: "AMG_ERR_TIMEOUT",

@@ -51,10 +51,13 @@ struct FcgState {
   double g;       // gamma_i / rho_{i-1}
 };
 
+struct PairCtl;  // paired-pass kernel control word (pair.cuh)
+
 struct Level {
   int n = 0;
   int64_t nnz = 0;
   int maxrow = 0;            // longest row (nonzeros)
+  int bw = 0;                // bandwidth: max |i - j| over the stored entries
   int R = 256;               // tile height of the row kernels with this level's V-cycle value type
   int Rd = 256;              // tile height with FP64 values (outer kernels, amg_spmv)
   bool pipe = false;         // every tile fits a pipeline stage (V-cycle value type)
@@ -72,6 +75,8 @@ struct Level {
   int32_t* mptr = nullptr;   // members of each next-level row (ascending)
   int32_t* mem = nullptr;
   bool lowp = false;         // this level runs in float inside the V-cycle
+  PairCtl* pctl = nullptr;   // paired-pass kernel state (pair.cuh): control word and per-tile counters
+  unsigned* pcnt = nullptr;
   // work vectors (double or float according to lowp)
   void* r = nullptr;         // level input (restricted residual), levels > 0
   void* za = nullptr;
@@ -114,6 +119,8 @@ struct amg_handle {
   int small_rows = 0;          // levels with fewer rows use the non-pipelined tiled kernels
   int min_tpr = 1;             // tuning hook: least threads per row of the pipelined kernels
   int fuse = 1;                // restriction and prolongation fused into the coarse level's first / last sweep
+  int use_pair = 0;            // consecutive row passes in one launch (0 never: measured slower; 1 on levels with room for the lag; 2 always)
+  int pair_slack = -1;         // tiles of lag beyond the halo (-1: two rounds of the grid)
   int kb = AMG_MAXL;           // first level of the fused bottom (nl: none)
   BotPlan* bot = nullptr;      // launch arguments of the fused bottom (solve.cu)
   long long suitor_cap = -1;   // test hook: step cap of the matching loop (-1: proof-level bound)

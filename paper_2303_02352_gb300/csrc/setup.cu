@@ -484,6 +484,13 @@ __global__ void k_maxrow(int n, const int32_t* __restrict__ rp, int* out) {
   if (i < n) atomicMax(out, rp[i + 1] - rp[i]);
 }
 
+// bandwidth max |i - j| (columns are sorted: the first and last entry decide)
+__global__ void k_bandwidth(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || rp[i + 1] == rp[i]) return;
+  atomicMax(out, max(i - ci[rp[i]], ci[rp[i + 1] - 1] - i));
+}
+
 // l1-Jacobi: M_ii = sum_j |a_ij| (CSR order), D_i = omega_i / M_ii
 __global__ void k_l1(int n, const int32_t* __restrict__ rp, const double* __restrict__ v,
                      const double* __restrict__ omega, double* __restrict__ l1, double* __restrict__ dinv,
@@ -781,6 +788,12 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
     if (st0 != AMG_OK) return st0;
     AMG_CK(h, cudaMemsetAsync(h->dev_flags, 0, sizeof(int), s));
     L.maxrow = mr;
+    k_bandwidth<<<amg_blocks(L.n), AMG_BLOCK, 0, s>>>(L.n, L.rp, L.ci, h->dev_flags);
+    int bwd = 0;
+    st0 = sync_read(h, h->dev_flags, &bwd);
+    if (st0 != AMG_OK) return st0;
+    AMG_CK(h, cudaMemsetAsync(h->dev_flags, 0, sizeof(int), s));
+    L.bw = bwd;
     const int vb = L.lowp ? ((h->p.precision == AMG_FP32_BF16FINE && k == 0) ? 2 : 4) : 8;
     L.Rd = amg_tile_rows(mr, 8);
     L.R = amg_tile_rows(mr, vb);
@@ -835,6 +848,8 @@ extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* str
   // AMG_STAGES pipeline depth, AMG_BOTTOM=0/1/2 bottom levels as separate
   // launches / in one cluster launch / by the owner-spread rule (default),
   // AMG_FUSE=0 restriction and prolongation as separate kernels,
+  // AMG_PAIR=0/1/2 paired row passes never / where they pay / always,
+  // AMG_PAIR_SLACK lag of the paired passes beyond the halo (tiles),
   // AMG_SMALL_ROWS, AMG_MIN_TPR row-kernel forms,
   // AMG_SUITOR_CAP step cap of the matching loop,
   // AMG_FAIL_ALLOC_AFTER make the k-th device allocation of the handle fail
@@ -843,6 +858,8 @@ extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* str
   if (const char* e = getenv("AMG_SMALL_ROWS")) h->small_rows = atoi(e);
   if (const char* e = getenv("AMG_MIN_TPR")) h->min_tpr = atoi(e);
   if (const char* e = getenv("AMG_FUSE")) h->fuse = atoi(e);
+  if (const char* e = getenv("AMG_PAIR")) h->use_pair = atoi(e);
+  if (const char* e = getenv("AMG_PAIR_SLACK")) h->pair_slack = atoi(e);
   if (const char* e = getenv("AMG_FAIL_ALLOC_AFTER")) h->fail_alloc_after = atoi(e);
   if (const char* e = getenv("AMG_PIPE")) h->use_pipe = atoi(e);
   if (const char* e = getenv("AMG_STAGES")) h->stages = atoi(e);

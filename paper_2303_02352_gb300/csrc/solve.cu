@@ -464,6 +464,7 @@ int amg_num_sms() {
 }
 
 #include "rows.cuh"
+#include "pair.cuh"
 #include "bottom.cuh"
 
 // ---------------------------------------------------------------------------
@@ -542,6 +543,38 @@ static void launch_resid(cudaStream_t s, const Level& L, const MT* vals, const V
   }
   const int nb = (L.n + R - 1) / R;
   DISPATCH_R(R, (amg_launch(k_resid<TR, MT, VT>, dim3(nb), dim3(TR), 0, s, L.n, L.rp, L.ci, vals, r, z, t, skip)));
+}
+
+// two consecutive row passes of level L in one launch (pair.cuh): a sweep
+// z1 = z0 + D (r - A z0), then MODE2 on z1 into out.  false (nothing
+// launched) where the level runs the non-pipelined kernels, has no pairing
+// state, or (use_pair = 1) has too few tiles for the lag to leave room for
+// reuse through L2.
+template <int MODE2, typename MT, typename VT, typename OT>
+static bool launch_pair(amg_handle* h, cudaStream_t s, const Level& L, const MT* vals, const VT* dinv, const VT* r,
+                        const VT* z0, VT* z1, OT* out, const int* skip, bool force = false) {
+  if (!(h->use_pair || force) || !L.pipe || !L.pctl) return false;
+  const int R = L.R;
+  const int ntiles = (L.n + R - 1) / R;
+  const int halo = (L.bw + R - 1) / R;
+  int grid = 0;
+  DISPATCH_TPR(PIPE_CONSUMERS / R, (grid = pair_grid<TP, PAIR_STAGES, MODE2, MT, VT, OT>(L.n)));
+  const int lag = halo + PAIR_CHUNK + 1 + (h->pair_slack >= 0 ? h->pair_slack : 2 * grid);
+  if (h->use_pair == 1 && !force && ntiles < 2 * lag) return false;
+  PairArgs<MT, VT, OT> a{L.n, L.rp, L.ci, vals, dinv, r, z0, z1, out, skip, h->dev_flags, L.pctl, L.pcnt, halo, lag};
+  DISPATCH_TPR(PIPE_CONSUMERS / R, (launch_pair_tpr<TP, PAIR_STAGES, MODE2, MT, VT, OT>(s, a)));
+  return true;
+}
+
+// zeroes the paired-pass state of every level (after a bounded wait expired)
+static void pair_reset(amg_handle* h) {
+  for (int k = 0; k < h->nl; ++k) {
+    Level& L = h->L[k];
+    if (!L.pctl) continue;
+    const int ntiles = (L.n + L.R - 1) / L.R;
+    cudaMemsetAsync(L.pctl, 0, sizeof(PairCtl), h->stream);
+    cudaMemsetAsync(L.pcnt, 0, sizeof(unsigned) * (size_t)ntiles, h->stream);
+  }
 }
 
 // outer kernels on level 0 (FP64 values)
@@ -966,16 +999,30 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out, bool firs
   const double rc_bytes = rcopy ? sx * n : 0.0;
   // pre-smoothing from zero
   VT* cur = za;
+  bool resid_done = false;
   if (h->p.pre_sweeps > 0) {
     if (!first_done) {
       amg_launch(k_first<RT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, dinv, rin, rcopy, za, R.skip);
       R.add(sr * n + 2.0 * sx * n + rc_bytes);
     }
-    for (int sw = 1; sw < h->p.pre_sweeps; ++sw) {
+    // sweeps 2 .. pre, paired where the level allows (two sweeps, or the last
+    // sweep with the residual); byte counts per pass as for separate launches
+    for (int left = h->p.pre_sweeps - 1; left > 0;) {
       VT* nxt = cur == za ? zb : za;
-      launch_sweep<MT, VT, VT>(R.s, L, vals, dinv, r, cur, nxt, R.skip, h->dev_flags, h->stages);
-      R.add(row_pass(L, sv) + 4.0 * sx * n);
-      cur = nxt;
+      if (left >= 2 && launch_pair<PM_SWEEP, MT, VT, VT>(h, R.s, L, vals, dinv, r, cur, nxt, cur, R.skip)) {
+        R.add(2.0 * (row_pass(L, sv) + 4.0 * sx * n));
+        left -= 2;
+      } else if (left == 1 && launch_pair<PM_RESID, MT, VT, VT>(h, R.s, L, vals, dinv, r, cur, nxt, t, R.skip)) {
+        R.add(row_pass(L, sv) + 4.0 * sx * n + row_pass(L, sv) + 3.0 * sx * n);
+        cur = nxt;
+        left = 0;
+        resid_done = true;
+      } else {
+        launch_sweep<MT, VT, VT>(R.s, L, vals, dinv, r, cur, nxt, R.skip, h->dev_flags, h->stages);
+        R.add(row_pass(L, sv) + 4.0 * sx * n);
+        cur = nxt;
+        --left;
+      }
     }
   } else {
     if (rcopy) {
@@ -986,8 +1033,10 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out, bool firs
     R.add(sx * n);
   }
   // residual, restriction, coarse correction, prolongation
-  launch_resid<MT, VT>(R.s, L, vals, r, cur, t, R.skip, h->dev_flags, h->stages);
-  R.add(row_pass(L, sv) + 3.0 * sx * n);
+  if (!resid_done) {
+    launch_resid<MT, VT>(R.s, L, vals, r, cur, t, R.skip, h->dev_flags, h->stages);
+    R.add(row_pass(L, sv) + 3.0 * sx * n);
+  }
   rec_child<VT>(R, k, t, cur);
   // post-smoothing
   const int post = h->p.post_sweeps;
@@ -998,6 +1047,19 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out, bool firs
   }
   for (int sw = 0; sw < post; ++sw) {
     VT* nxt = cur == za ? zb : za;
+    // two sweeps in one launch where the level allows (not for a last sweep
+    // that prolongs into the finer level)
+    if (post - sw >= 2 && !(post - sw == 2 && pro)) {
+      const bool last = post - sw == 2 && final_out;
+      const bool paired = last ? launch_pair<PM_SWEEP, MT, VT, double>(h, R.s, L, vals, dinv, r, cur, nxt, final_out, R.skip)
+                               : launch_pair<PM_SWEEP, MT, VT, VT>(h, R.s, L, vals, dinv, r, cur, nxt, cur, R.skip);
+      if (paired) {
+        R.add(2.0 * (row_pass(L, sv) + 4.0 * sx * n) + (last ? 8.0 * n - sx * n : 0.0));
+        ++sw;
+        if (last) return nullptr;
+        continue;
+      }
+    }
     if (sw == post - 1 && final_out) {
       launch_sweep<MT, VT, double>(R.s, L, vals, dinv, r, cur, final_out, R.skip, h->dev_flags, h->stages);
       R.add(row_pass(L, sv) + 3.0 * sx * n + 8.0 * n);
@@ -1084,6 +1146,7 @@ extern "C" amg_status amg_kernel_bytes(const amg_handle* h, int32_t which, int32
                           : row_pass(C, val_bytes(C)) + 4.0 * sc * nc + prolong_fused_bytes(L, C);
       return AMG_OK;
     }
+    case 8: *bytes = row_pass(L, sv) + 5.0 * sx * n; return AMG_OK;  // matrix once; z0, r, D read; z1, z2 written
     case 4: *bytes = level == 0 ? bytes_spmv_dots(L) : 0.0; return level == 0 ? AMG_OK : AMG_ERR_INVALID_ARG;
     case 5: *bytes = level == 0 ? bytes_axpy(L) : 0.0; return level == 0 ? AMG_OK : AMG_ERR_INVALID_ARG;
     default: return AMG_ERR_INVALID_ARG;
@@ -1105,6 +1168,13 @@ amg_status amg_prepare_solve(amg_handle* h) {
         (!(L.e = amg_alloc(h, es * L.n)) || !(L.r2 = amg_alloc(h, es * L.n))))
       return amg_fail(h, AMG_ERR_OOM, "W-cycle vectors of level %d", k);
     if (k == 0 && L.lowp) AMG_ALLOC(h, L.r0f, float, L.n);
+    if (L.pipe && !L.pctl) {  // paired-pass state (zero: epoch 0, watermark 0)
+      const size_t ntiles = ((size_t)L.n + L.R - 1) / L.R;
+      AMG_ALLOC(h, L.pctl, PairCtl, 1);
+      AMG_ALLOC(h, L.pcnt, unsigned, ntiles);
+      AMG_CK(h, cudaMemsetAsync(L.pctl, 0, sizeof(PairCtl), h->stream));
+      AMG_CK(h, cudaMemsetAsync(L.pcnt, 0, sizeof(unsigned) * ntiles, h->stream));
+    }
   }
   AMG_ALLOC(h, h->b, double, n);
   AMG_ALLOC(h, h->u, double, n);
@@ -1210,7 +1280,10 @@ static amg_status check_device_flags(amg_handle* h) {
   AMG_CK(h, cudaStreamSynchronize(h->stream));
   if (!f) return AMG_OK;
   AMG_CK(h, cudaMemsetAsync(h->dev_flags, 0, sizeof(int), h->stream));
-  if (f & ST_TIMEOUT) return amg_fail(h, AMG_ERR_TIMEOUT, "a bounded wait of a row kernel expired");
+  if (f & ST_TIMEOUT) {
+    pair_reset(h);  // the paired-pass counters of an interrupted launch are behind
+    return amg_fail(h, AMG_ERR_TIMEOUT, "a bounded wait of a row kernel expired");
+  }
   return amg_fail(h, AMG_ERR_CUDA, "device error flags %d", f);
 }
 
@@ -1436,6 +1509,21 @@ static amg_status launch_one(amg_handle* h, int which, int k) {
                                                   (float*)C.zb, skip, h->dev_flags, L, L.za, true);
         if (!ok) return amg_fail(h, AMG_ERR_INVALID_ARG, "level %d runs the non-pipelined kernels", k + 1);
       }
+      break;
+    }
+    case 8: {  // two sweeps in one launch (za -> zb -> za)
+      const double* r64 = k == 0 ? h->r : (const double*)L.r;
+      bool ok;
+      if (!L.lowp)
+        ok = launch_pair<PM_SWEEP, double, double, double>(h, s, L, L.v, L.dinv, r64, (const double*)L.za, (double*)L.zb,
+                                                           (double*)L.za, skip, true);
+      else if (L.vb)
+        ok = launch_pair<PM_SWEEP, bf16, float, float>(h, s, L, L.vb, L.dinvf, k == 0 ? L.r0f : (const float*)L.r,
+                                                       (const float*)L.za, (float*)L.zb, (float*)L.za, skip, true);
+      else
+        ok = launch_pair<PM_SWEEP, float, float, float>(h, s, L, L.vf, L.dinvf, k == 0 ? L.r0f : (const float*)L.r,
+                                                        (const float*)L.za, (float*)L.zb, (float*)L.za, skip, true);
+      if (!ok) return amg_fail(h, AMG_ERR_INVALID_ARG, "level %d runs the non-pipelined kernels", k);
       break;
     }
     case 4:

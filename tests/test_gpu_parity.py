@@ -366,6 +366,56 @@ def test_fused_kernel_timing_entries():
             g.time_kernel(amg.K_RESTRICT_FIRST, g.num_levels - 1, reps=1)
 
 
+PAIR_PROBLEMS = {
+    "poisson32": lambda: W.poisson7(32),
+    "poisson64": lambda: W.poisson7(64),
+    "poisson13": lambda: W.poisson7(13),
+    "diff27_24": lambda: W.diffusion27(24, 2.0, 3),
+    "laplace1d": lambda: W.laplace1d(30001),
+}
+
+
+@pytest.mark.parametrize("name", list(PAIR_PROBLEMS))
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("slack", ["0", "3", "40"])
+def test_paired_passes_bitwise(name, prec, slack, monkeypatch):
+    """Two row passes in one launch (the second reading the first's results as
+    they complete, tile by tile) give the single-pass results bit for bit, for
+    lags from the halo alone (second pass right behind the first) upwards."""
+    A = PAIR_PROBLEMS[name]()
+    r = W.random_vector(A.n, 31)
+    monkeypatch.setenv("AMG_PAIR", "0")
+    g0 = G(A, precision=prec)
+    z0 = g0.vcycle(r).cpu().numpy()
+    monkeypatch.setenv("AMG_PAIR", "2")
+    monkeypatch.setenv("AMG_PAIR_SLACK", slack)
+    g1 = G(A, precision=prec)
+    for _ in range(3):  # repeated launches: the counters carry over between launches
+        assert np.array_equal(g1.vcycle(r).cpu().numpy(), z0)
+    if prec == 0 and name in ("poisson32", "diff27_24"):
+        b = W.rhs_from_solution(A, W.random_vector(A.n, 5))
+        r0, r1 = g0.pcg_solve(b), g1.pcg_solve(b)
+        assert r0["iters"] == r1["iters"]
+        assert np.array_equal(r0["x"].cpu().numpy(), r1["x"].cpu().numpy())
+
+
+def test_paired_kernel_timing_entry(monkeypatch):
+    from paper_2303_02352_gb300 import amg
+    A = W.poisson7(40)
+    for prec in (0, 1, 2):
+        g = G(A, precision=prec)
+        assert g.time_kernel(amg.K_SWEEP_PAIR, 0, reps=3) > 0.0
+        assert g.kernel_bytes(amg.K_SWEEP_PAIR, 0) > 0.0
+    # the state stays consistent for the V-cycle after standalone launches
+    r = W.random_vector(A.n, 2)
+    monkeypatch.setenv("AMG_PAIR", "2")
+    monkeypatch.setenv("AMG_PAIR_SLACK", "1")
+    g = G(A)
+    z0 = g.vcycle(r).cpu().numpy()
+    g.time_kernel(amg.K_SWEEP_PAIR, 0, reps=5)
+    assert np.array_equal(g.vcycle(r).cpu().numpy(), z0)
+
+
 @pytest.mark.parametrize("np_", [2, 5])
 def test_decoupled_aggregation_parity(np_):
     A = W.diffusion27(12, 2.0, 21)
