@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pair(const PairArg
   pdl_trigger();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   auto* P = reinterpret_cast<PipeSmem<MT, S>*>(smem_raw);
-  constexpr int VE = PipeTile<MT>::VE;
+  constexpr int VE = PipeTile<MT, 1>::VE;
   constexpr int NCW = PIPE_CONSUMERS / 32;
   const int n = a.n;
   const int ntiles = (n + R - 1) / R;
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pair(const PairArg
         }
       }
       const int av = p0 & ~(VE - 1), ac = p0 & ~3;
-      const PipeTile<MT>& T = P->st[stage];
+      const PipeTile<MT, 1>& T = P->st[stage];
       VT s = 0;
       if (phase == 0) {
 #pragma unroll 8

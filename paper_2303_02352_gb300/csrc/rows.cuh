@@ -23,17 +23,19 @@
 // PIPE_CONSUMERS-row tile of a 7-point stencil fits with little slack (smaller
 // stages mean more resident blocks per multiprocessor, which is what the row
 // kernels need)
-template <typename MT>
+// SB scales the stage: SB = 4 (FP64 only) holds 256 rows of up to 32 entries,
+// so long-row levels keep one thread per row (see launch_rows)
+template <typename MT, int SB = 1>
 struct PipeTile {
   static constexpr int VE = 16 / (int)sizeof(MT);
-  static constexpr int CAP = amg_pipe_tile_bytes((int)sizeof(MT)) / ((int)sizeof(MT) + 4);
+  static constexpr int CAP = amg_pipe_tile_bytes((int)sizeof(MT)) * SB / ((int)sizeof(MT) + 4);
   MT v[CAP + 2 * VE];
   int32_t c[CAP + 8];
 };
 
-template <typename MT, int S>
+template <typename MT, int S, int SB = 1>
 struct PipeSmem {
-  PipeTile<MT> st[S];
+  PipeTile<MT, SB> st[S];
   unsigned long long full[S];   // producer -> consumers: the stage holds the tile
   unsigned long long empty[S];  // consumers -> producer: every consumer warp has read it
 };
@@ -170,12 +172,19 @@ __device__ __forceinline__ bool mbar_wait_warp(unsigned long long* bar, uint32_t
 // expect_tx plus the bytes of the two bulk copies) and an "empty" barrier (one
 // arrival per consumer warp once it has read the stage).  No block-wide
 // barrier inside the tile loop: warps drift up to S tiles apart.
-template <int TPR, int S, int MODE, typename MT, typename VT, typename OT>
+//
+// NG > 1 splits the consumer warps into NG groups that take the block's tiles
+// in turn (group g: tiles g, g + NG, ...): tiles of R = PIPE_CONSUMERS / NG /
+// TPR rows, S stages in flight, each stage read by one group.  Long rows then
+// keep one thread per row with more, smaller stages in flight.
+template <int TPR, int S, int MODE, typename MT, typename VT, typename OT, int SB = 1, int NG = 1>
 __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs<MT, VT, OT> a) {
-  constexpr int R = PIPE_CONSUMERS / TPR;
+  static_assert(S % NG == 0, "each stage is read by one group");
+  constexpr int CG = PIPE_CONSUMERS / NG;  // consumer threads per group
+  constexpr int R = CG / TPR;
   pdl_trigger();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  auto* P = reinterpret_cast<PipeSmem<MT, S>*>(smem_raw);
+  auto* P = reinterpret_cast<PipeSmem<MT, S, SB>*>(smem_raw);
   __shared__ double red[96];
   constexpr int VE = PipeTile<MT>::VE;
   constexpr int NCW = PIPE_CONSUMERS / 32;  // consumer warps
@@ -187,7 +196,7 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&P->full[s], 1);
-      mbar_init(&P->empty[s], NCW);
+      mbar_init(&P->empty[s], NCW / NG);
     }
     mbar_fence_init();
   }
@@ -257,13 +266,14 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
     __syncwarp();  // reconverge before the block-wide reduction below
   } else {
     // ---------------- consumer warps ----------------
-    for (int k = 0;; ++k) {
+    const int grp = (int)threadIdx.x / CG, tg = (int)threadIdx.x % CG;  // group, thread in group
+    for (int k = grp;; k += NG) {
       const int tile = blockIdx.x + k * G;
       if (tile >= ntiles) break;
       const int stage = k % S;
       const int row0 = tile * R, row1 = min(row0 + R, n);
-      const int sub = (int)threadIdx.x % TPR;  // lane within the row's group
-      const int row = row0 + (int)threadIdx.x / TPR;
+      const int sub = tg % TPR;  // lane within the row's group
+      const int row = row0 + tg / TPR;
       const bool live = row < row1;
       const bool lead = live && sub == 0;      // the lane that finishes the row
       const int p0 = __ldg(&a.rp[row0]);
@@ -294,7 +304,7 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
         break;
       }
       const int av = p0 & ~(VE - 1), ac = p0 & ~3;
-      const PipeTile<MT>& T = P->st[stage];
+      const PipeTile<MT, SB>& T = P->st[stage];
       VT s = 0;
 #pragma unroll 8
       for (int q = q0; q < q1; q += TPR) s += (VT)to_acc(T.v[q - av]) * __ldg(&a.x[T.c[q - ac]]);
@@ -360,12 +370,12 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
 
 // grid of a persistent pipelined kernel: one wave of resident blocks, at most
 // one block per tile
-template <int TPR, int S, int MODE, typename MT, typename VT, typename OT>
+template <int TPR, int S, int MODE, typename MT, typename VT, typename OT, int SB = 1, int NG = 1>
 static int pipe_grid(int n) {
   static int bps = -1;
-  constexpr int smem = (int)sizeof(PipeSmem<MT, S>);
-  constexpr int R = PIPE_CONSUMERS / TPR;
-  auto kern = k_rows_pipe<TPR, S, MODE, MT, VT, OT>;
+  constexpr int smem = (int)sizeof(PipeSmem<MT, S, SB>);
+  constexpr int R = PIPE_CONSUMERS / NG / TPR;
+  auto kern = k_rows_pipe<TPR, S, MODE, MT, VT, OT, SB, NG>;
   if (bps < 0) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -378,9 +388,9 @@ static int pipe_grid(int n) {
   return ntiles < g ? ntiles : g;
 }
 
-template <int TPR, int S, int MODE, typename MT, typename VT, typename OT>
+template <int TPR, int S, int MODE, typename MT, typename VT, typename OT, int SB = 1, int NG = 1>
 static void launch_pipe(cudaStream_t s, const RowArgs<MT, VT, OT>& a) {
-  const int grid = pipe_grid<TPR, S, MODE, MT, VT, OT>(a.n);
-  constexpr int smem = (int)sizeof(PipeSmem<MT, S>);
-  amg_launch(k_rows_pipe<TPR, S, MODE, MT, VT, OT>, dim3(grid), dim3(PIPE_CONSUMERS + 32), (size_t)smem, s, a);
+  const int grid = pipe_grid<TPR, S, MODE, MT, VT, OT, SB, NG>(a.n);
+  constexpr int smem = (int)sizeof(PipeSmem<MT, S, SB>);
+  amg_launch(k_rows_pipe<TPR, S, MODE, MT, VT, OT, SB, NG>, dim3(grid), dim3(PIPE_CONSUMERS + 32), (size_t)smem, s, a);
 }

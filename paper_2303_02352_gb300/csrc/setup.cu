@@ -805,6 +805,27 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
     L.pipe = h->use_pipe && big && (int64_t)Rp * mr <= amg_pipe_tile_bytes(vb) / (vb + 4);
     if (L.piped) L.Rd = Rpd;
     if (L.pipe) L.R = Rp;
+    // FP64 values and rows too long for one thread per row in a normal stage:
+    // a 4x stage holds 256 rows of up to 32 entries (fewer FP64 instructions
+    // per row than several threads per row with a shuffle reduction; FP64
+    // issue limits these kernels on this part)
+    // forms: 2 = 2x stages, 128 rows, 2 threads per row; 4 = 4x stages, 256
+    // rows, one thread per row; 5 = two consumer groups, four 2x stages, 128
+    // rows, one thread per row
+    const int sbig = h->use_big;
+    const int rbig = sbig == 4 ? 256 : 128;                          // rows per tile
+    const int scale = sbig == 4 ? 4 : 2;                             // stage scale
+    const int tpr_big = sbig == 2 ? 2 : 1;
+    const bool big_rows = (sbig == 2 || sbig == 4 || sbig == 5) && h->min_tpr <= tpr_big &&
+                          (int64_t)rbig * mr <= (int64_t)amg_pipe_tile_bytes(8) * scale / 12;
+    if (L.pipe && vb == 8 && L.R < rbig && big_rows) {
+      L.R = rbig;
+      L.sb = sbig;
+    }
+    if (L.piped && L.Rd < rbig && big_rows) {
+      L.Rd = rbig;
+      L.sbd = sbig;
+    }
     AMG_ALLOC(h, L.l1, double, L.n);
     AMG_ALLOC(h, L.dinv, double, L.n);
     if (L.lowp) {
@@ -848,6 +869,7 @@ extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* str
   // AMG_STAGES pipeline depth, AMG_BOTTOM=0/1/2 bottom levels as separate
   // launches / in one cluster launch / by the owner-spread rule (default),
   // AMG_FUSE=0 restriction and prolongation as separate kernels,
+  // AMG_BIG=0 no 4x stages for FP64 long-row levels,
   // AMG_PAIR=0/1/2 paired row passes never / where they pay / always,
   // AMG_PAIR_SLACK lag of the paired passes beyond the halo (tiles),
   // AMG_SMALL_ROWS, AMG_MIN_TPR row-kernel forms,
@@ -859,6 +881,7 @@ extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* str
   if (const char* e = getenv("AMG_MIN_TPR")) h->min_tpr = atoi(e);
   if (const char* e = getenv("AMG_FUSE")) h->fuse = atoi(e);
   if (const char* e = getenv("AMG_PAIR")) h->use_pair = atoi(e);
+  if (const char* e = getenv("AMG_BIG")) h->use_big = atoi(e);
   if (const char* e = getenv("AMG_PAIR_SLACK")) h->pair_slack = atoi(e);
   if (const char* e = getenv("AMG_FAIL_ALLOC_AFTER")) h->fail_alloc_after = atoi(e);
   if (const char* e = getenv("AMG_PIPE")) h->use_pipe = atoi(e);

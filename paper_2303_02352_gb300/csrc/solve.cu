@@ -489,8 +489,25 @@ int amg_num_sms() {
     default: { constexpr int TP = 32; CALL; } break;    \
   }
 
+// sb = 2 / 4: FP64 level with long rows in 2x / 4x stages (R = 128 with two
+// threads per row / R = 256 with one); sb = 5: two consumer groups taking
+// tiles in turn, R = 128 rows with one thread per row, four 2x stages
 template <int MODE, typename MT, typename VT, typename OT>
-static void launch_rows(cudaStream_t s, int R, int /*stages*/, const RowArgs<MT, VT, OT>& a) {
+static void launch_rows(cudaStream_t s, int R, int sb, const RowArgs<MT, VT, OT>& a) {
+  if constexpr (sizeof(MT) == 8) {
+    if (sb == 5) {
+      launch_pipe<1, 4, MODE, MT, VT, OT, 2, 2>(s, a);
+      return;
+    }
+    if (sb == 4) {
+      launch_pipe<1, 2, MODE, MT, VT, OT, 4>(s, a);
+      return;
+    }
+    if (sb == 2) {
+      launch_pipe<2, 2, MODE, MT, VT, OT, 2>(s, a);
+      return;
+    }
+  }
   DISPATCH_TPR(PIPE_CONSUMERS / R, (launch_pipe<TP, 2, MODE, MT, VT, OT>(s, a)));
 }
 
@@ -500,7 +517,7 @@ static void launch_sweep(cudaStream_t s, const Level& L, const MT* vals, const V
   const int R = L.R;
   if (L.pipe) {
     RowArgs<MT, VT, OT> a{L.n, L.rp, L.ci, vals, z, dinv, r, nullptr, nullptr, out, skip, nullptr, nullptr, nullptr, flags};
-    launch_rows<PM_SWEEP>(s, R, stages, a);
+    launch_rows<PM_SWEEP>(s, R, L.sb, a);
     return;
   }
   const int nb = (L.n + R - 1) / R;
@@ -509,7 +526,12 @@ static void launch_sweep(cudaStream_t s, const Level& L, const MT* vals, const V
 
 // grid of the pipelined row kernel of `MODE` on a level with tiles of R rows
 template <int MODE, typename MT, typename VT, typename OT>
-static int rows_grid(int R, int n) {
+static int rows_grid(int R, int sb, int n) {
+  if constexpr (sizeof(MT) == 8) {
+    if (sb == 5) return pipe_grid<1, 4, MODE, MT, VT, OT, 2, 2>(n);
+    if (sb == 4) return pipe_grid<1, 2, MODE, MT, VT, OT, 4>(n);
+    if (sb == 2) return pipe_grid<2, 2, MODE, MT, VT, OT, 2>(n);
+  }
   int g = 0;
   DISPATCH_TPR(PIPE_CONSUMERS / R, (g = pipe_grid<TP, 2, MODE, MT, VT, OT>(n)));
   return g;
@@ -525,10 +547,10 @@ static bool launch_sweep_prolong(cudaStream_t s, const Level& C, const MT* vals,
                                  VT* out, const int* skip, int* flags, const Level& F, void* zf, bool any_size = false) {
   if (!C.pipe) return false;
   const int tiles = (C.n + C.R - 1) / C.R;
-  if (!any_size && rows_grid<PM_SWEEP_PROLONG, MT, VT, VT>(C.R, C.n) < tiles) return false;
+  if (!any_size && rows_grid<PM_SWEEP_PROLONG, MT, VT, VT>(C.R, C.sb, C.n) < tiles) return false;
   RowArgs<MT, VT, VT> a{C.n, C.rp, C.ci, vals, z, dinv, r, nullptr, nullptr, out, skip, nullptr, nullptr, nullptr, flags,
                         F.mptr, F.mem, zf, F.lowp ? 0 : 1};
-  launch_rows<PM_SWEEP_PROLONG>(s, C.R, 2, a);
+  launch_rows<PM_SWEEP_PROLONG>(s, C.R, C.sb, a);
   return true;
 }
 
@@ -538,7 +560,7 @@ static void launch_resid(cudaStream_t s, const Level& L, const MT* vals, const V
   const int R = L.R;
   if (L.pipe) {
     RowArgs<MT, VT, VT> a{L.n, L.rp, L.ci, vals, z, nullptr, r, nullptr, nullptr, t, skip, nullptr, nullptr, nullptr, flags};
-    launch_rows<PM_RESID>(s, R, stages, a);
+    launch_rows<PM_RESID>(s, R, L.sb, a);
     return;
   }
   const int nb = (L.n + R - 1) / R;
@@ -553,7 +575,7 @@ static void launch_resid(cudaStream_t s, const Level& L, const MT* vals, const V
 template <int MODE2, typename MT, typename VT, typename OT>
 static bool launch_pair(amg_handle* h, cudaStream_t s, const Level& L, const MT* vals, const VT* dinv, const VT* r,
                         const VT* z0, VT* z1, OT* out, const int* skip, bool force = false) {
-  if (!(h->use_pair || force) || !L.pipe || !L.pctl) return false;
+  if (!(h->use_pair || force) || !L.pipe || !L.pctl || L.sb != 1) return false;
   const int R = L.R;
   const int ntiles = (L.n + R - 1) / R;
   const int halo = (L.bw + R - 1) / R;
@@ -584,7 +606,7 @@ static void launch_dots(amg_handle* h, cudaStream_t s) {
   if (L.piped) {
     RowArgs<double, double, double> a{L.n, L.rp, L.ci, L.v, h->w, nullptr, h->r, nullptr, h->q, h->v,
                                       nullptr, h->st, h->partial, h->counter, h->dev_flags};
-    launch_rows<PM_DOTS>(s, L.Rd, h->stages, a);
+    launch_rows<PM_DOTS>(s, L.Rd, L.sbd, a);
     return;
   }
   DISPATCH_R(L.Rd, (k_fcg_spmv_dots<TR><<<h->red_grid, TR, 0, s>>>(L.n, L.rp, L.ci, L.v, h->w, h->r, h->q, h->v, h->st,
@@ -600,7 +622,7 @@ static void launch_fcg_resid(amg_handle* h, cudaStream_t s) {
     RowArgs<double, double, double> a{L.n, L.rp, L.ci, L.v, h->u, nullptr, nullptr, h->b, nullptr,
                                       MODE == RES_NORM ? nullptr : h->r, nullptr, h->st, h->partial, h->counter,
                                       h->dev_flags};
-    launch_rows<PM>(s, L.Rd, h->stages, a);
+    launch_rows<PM>(s, L.Rd, L.sbd, a);
     return;
   }
   DISPATCH_R(L.Rd, (k_fcg_resid<TR, MODE><<<h->red_grid, TR, 0, s>>>(L.n, L.rp, L.ci, L.v, h->b, h->u,

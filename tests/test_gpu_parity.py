@@ -366,6 +366,27 @@ def test_fused_kernel_timing_entries():
             g.time_kernel(amg.K_RESTRICT_FIRST, g.num_levels - 1, reps=1)
 
 
+@pytest.mark.parametrize("form", ["0", "2", "4", "5"])
+@pytest.mark.parametrize("name", ["diff27_12", "diff27_24"])
+def test_long_row_kernel_forms(form, name, monkeypatch):
+    """FP64 levels with long rows: one thread per row in 4x stages, two
+    threads per row in 2x stages, two consumer groups over four 2x stages, or
+    the default tile fitting -- all against the oracle."""
+    A = PAIR_PROBLEMS[name]() if name in PAIR_PROBLEMS else PROBLEMS[name]()
+    monkeypatch.setenv("AMG_BIG", form)
+    g, o = G(A), O.Hierarchy(A)
+    r = W.random_vector(A.n, 8)
+    assert rel(g.vcycle(r).cpu().numpy(), o.vcycle(r)) < 1e-12
+    assert rel(g.spmv(0, r).cpu().numpy(), o.spmv(0, r)) < 1e-14
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 9))
+    rg, ro = g.pcg_solve(b), o.fcg(b)
+    assert abs(rg["iters"] - ro["iters"]) <= 1 and rg["true_rel_res"] < 1e-6
+    if rg["iters"] == ro["iters"]:
+        assert rel(rg["x"].cpu().numpy(), ro["x"]) < 1e-9
+    # low-precision hierarchy: the FP64 outer kernels take the long-row forms too
+    assert G(A, precision=1).pcg_solve(b)["true_rel_res"] < 1e-6
+
+
 PAIR_PROBLEMS = {
     "poisson32": lambda: W.poisson7(32),
     "poisson64": lambda: W.poisson7(64),
