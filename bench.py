@@ -389,7 +389,9 @@ def main():
                        "tol": args.tol,
                        "replicas": world, "l2": "inputs larger than L2 (level-0 matrix %.0f MB)" % (A.nnz * 12 / 1e6),
                        "levels": info["num_levels"], "n": info["n"], "nnz": info["nnz"],
-                       "opc": round(info["opc"], 4), "iters": iters},
+                       "opc": round(info["opc"], 4), "iters": iters,
+                       "kernel_forms": {"tile_rows": info["tile_rows"], "stage_scale": info["stage_scale"],
+                                        "fused_bottom_from_level": info["bottom_level"]}},
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(ach / peak, 4), "traffic": ncu_traffic(args.workload, args.precision),
                          "kernel": "l1-Jacobi sweep, level 0", "algorithmic_bytes_per_launch": by_sweep,

@@ -88,6 +88,9 @@ typedef struct {
   int32_t precision;          /* amg_precision of the hierarchy */
   double setup_match_ms;      /* setup time in the matching steps (weights, suitor, aggregation) */
   double setup_galerkin_ms;   /* setup time in the Galerkin products */
+  int32_t bottom_level;       /* first level of the fused bottom (one cluster launch); num_levels: none */
+  int32_t tile_rows[40];      /* rows per tile of the level's pipelined row kernels (0: non-pipelined) */
+  int32_t stage_scale[40];    /* pipeline stage size of those kernels in units of the standard stage */
 } amg_info_t;
 
 typedef struct amg_handle amg_handle;

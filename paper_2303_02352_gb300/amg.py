@@ -50,7 +50,8 @@ class amg_info_t(ctypes.Structure):
                 ("vcycle_bytes", ctypes.c_double), ("iteration_bytes", ctypes.c_double),
                 ("vcycle_launches", ctypes.c_int32), ("iteration_launches", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("setup_match_ms", ctypes.c_double),
-                ("setup_galerkin_ms", ctypes.c_double)]
+                ("setup_galerkin_ms", ctypes.c_double), ("bottom_level", ctypes.c_int32),
+                ("tile_rows", ctypes.c_int32 * 40), ("stage_scale", ctypes.c_int32 * 40)]
 
 
 _LIB = None
@@ -180,7 +181,9 @@ class Hierarchy:
                 "num_pairwise": inf.num_pairwise, "setup_ms": inf.setup_ms, "vcycle_bytes": inf.vcycle_bytes,
                 "iteration_bytes": inf.iteration_bytes, "vcycle_launches": inf.vcycle_launches,
                 "iteration_launches": inf.iteration_launches, "precision": inf.precision,
-                "setup_match_ms": inf.setup_match_ms, "setup_galerkin_ms": inf.setup_galerkin_ms}
+                "setup_match_ms": inf.setup_match_ms, "setup_galerkin_ms": inf.setup_galerkin_ms,
+                "bottom_level": inf.bottom_level, "tile_rows": list(inf.tile_rows[:L]),
+                "stage_scale": list(inf.stage_scale[:L])}
 
     @property
     def num_levels(self) -> int:

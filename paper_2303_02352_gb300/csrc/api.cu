@@ -46,6 +46,12 @@ extern "C" amg_status amg_info(const amg_handle* h, amg_info_t* info) {
   info->precision = h->p.precision;
   info->setup_match_ms = h->match_ms;
   info->setup_galerkin_ms = h->galerkin_ms;
+  info->bottom_level = h->kb < h->nl ? h->kb : h->nl;
+  for (int k = 0; k < h->nl && k < 40; ++k) {
+    const Level& L = h->L[k];
+    info->tile_rows[k] = L.pipe ? L.R : 0;
+    info->stage_scale[k] = L.pipe ? (L.sb == 5 ? 2 : L.sb) : 0;
+  }
   return AMG_OK;
 }
 

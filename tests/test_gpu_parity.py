@@ -387,6 +387,22 @@ def test_long_row_kernel_forms(form, name, monkeypatch):
     assert G(A, precision=1).pcg_solve(b)["true_rel_res"] < 1e-6
 
 
+def test_automatic_kernel_forms():
+    """The setup's automatic choices: one thread per row in 4x stages for the
+    27-point FP64 fine level, standard stages for 7-point, and the fused
+    bottom for the regular 7-point hierarchy but not for the irregular
+    27-point one (owner-spread rule)."""
+    p = G(W.poisson7(40)).info()
+    assert p["tile_rows"][0] == 256 and p["stage_scale"][0] == 1
+    assert p["bottom_level"] < p["num_levels"]
+    d = G(W.diffusion27(32, 2.0, 3)).info()
+    assert d["tile_rows"][0] == 256 and d["stage_scale"][0] == 4
+    assert d["bottom_level"] == d["num_levels"]
+    # low precision: the float fine level keeps standard stages
+    f = G(W.diffusion27(32, 2.0, 3), precision=1).info()
+    assert f["stage_scale"][0] == 1
+
+
 PAIR_PROBLEMS = {
     "poisson32": lambda: W.poisson7(32),
     "poisson64": lambda: W.poisson7(64),
