@@ -380,6 +380,34 @@ def main():
                               "vcycle_ms": g2.time_vcycle(reps=20), "vcycle_bytes": g2.info()["vcycle_bytes"]}
                 g2.close()
 
+    # the NEXT-row features on the same workload: plain CG (no preconditioner),
+    # the W-cycle, decoupled aggregation over row blocks, the setup split
+    extras = {}
+    if not args.no_extra:
+        def timed(hier, precond=True, maxit=1000):
+            x2 = torch.zeros_like(b)
+            hier.solve_into(b, x2.zero_(), args.tol, maxit, precond)
+            torch.cuda.synchronize()
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            r2 = hier.solve_into(b, x2.zero_(), args.tol, maxit, precond)
+            q1.record(stream)
+            torch.cuda.synchronize()
+            return {"ms": q0.elapsed_time(q1), "iters": r2["iters"], "true_rel_res": r2["true_rel_res"], **errors(x2)}
+
+        extras["cg_no_preconditioner"] = timed(g, precond=False, maxit=5000)
+        gw = amg.Hierarchy(A, precision=PRECISIONS[args.precision], cycle=2)
+        extras["w_cycle"] = {**timed(gw), "cycle_ms": gw.time_vcycle(reps=10)}
+        gw.close()
+        for parts in (8, 64):
+            gd = amg.Hierarchy(A, precision=PRECISIONS[args.precision], num_parts=parts)
+            di = gd.info()
+            extras["decoupled_%d_parts" % parts] = {**timed(gd), "levels": di["num_levels"], "n": di["n"],
+                                                   "opc": round(di["opc"], 4)}
+            gd.close()
+        extras["setup_split_ms"] = {"total": info["setup_ms"], "matching": info["setup_match_ms"],
+                                    "galerkin": info["setup_galerkin_ms"]}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -407,6 +435,7 @@ def main():
             "clocks": clk,
             "cpu_baseline": cpu,
             "forms": forms,
+            "extras": extras,
         }
         print(json.dumps(line), flush=True)
     g.close()
