@@ -72,6 +72,8 @@ typedef struct {
   int32_t num_parts;      /* decoupled aggregation (Sec. 4.1): match only inside this many
                              contiguous row blocks, as np tasks would (1 = global matching) */
   int32_t cycle;          /* Listing 1 cycle_type: 0 V-cycle, 2 W-cycle (0) */
+  int32_t relax_type;     /* Listing 1 relax_type: 4 l1-Jacobi, D = omega / sum_j |a_ij| (4);
+                             0 Jacobi, D = omega / a_ii; every level including the coarsest */
 } amg_params;
 
 typedef struct {

@@ -43,7 +43,7 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int) for name in (
         "aggr_steps", "max_levels", "coarse_size", "pre_sweeps", "post_sweeps",
-        "coarse_sweeps", "coarse_solver", "precision", "true_res_every", "num_parts", "cycle")]
+        "coarse_sweeps", "coarse_solver", "precision", "true_res_every", "num_parts", "cycle", "relax_type")]
 
 
 def _lib():
@@ -146,6 +146,7 @@ class Params:
     true_res_every: int = 50
     num_parts: int = 1
     cycle: int = 0
+    relax_type: int = 4
 
     def _c(self):
         p = _Params()

@@ -71,6 +71,7 @@ void orc_params_default(orc_params* p) {
   p->true_res_every = 50;
   p->num_parts = 1;
   p->cycle = 0;
+  p->relax_type = 4;     /* Listing 1: relax_type 4 (l1-Jacobi) */
 }
 
 static void* xcalloc(size_t n, size_t s) {
@@ -319,13 +320,18 @@ static void csr_free(ocsr* a) {
   memset(a, 0, sizeof(*a));
 }
 
+/* l1 row norms and D = omega / M with M_ii = sum_j |a_ij| (l1-Jacobi) or
+ * M_ii = a_ii (Jacobi, Listing 1 relax_type 0) */
 static void level_diag(orc_hier* h, int k) {
   ocsr* A = &h->A[k];
   for (int i = 0; i < A->n; ++i) {
-    double s = 0.0;
-    for (int32_t p = A->rp[i]; p < A->rp[i + 1]; ++p) s += fabs(A->v[p]);
+    double s = 0.0, d = 0.0;
+    for (int32_t p = A->rp[i]; p < A->rp[i + 1]; ++p) {
+      s += fabs(A->v[p]);
+      if (A->ci[p] == i) d = A->v[p];
+    }
     h->l1[k][i] = s;
-    h->dinv[k][i] = h->omega[k][i] / s;
+    h->dinv[k][i] = h->omega[k][i] / (h->p.relax_type == 0 ? d : s);
   }
 }
 
@@ -368,6 +374,7 @@ static void build_chol(orc_hier* h) {
 
 orc_hier* orc_setup(int n, const int32_t* rp, const int32_t* ci, const double* v, const orc_params* p) {
   if (n <= 0 || !rp || !ci || !v || !p) return NULL;
+  if (p->relax_type != 0 && p->relax_type != 4) return NULL;
   for (int i = 0; i < n; ++i)
     if (find_diag(rp, ci, i) < 0) return NULL;
   orc_hier* h = (orc_hier*)xcalloc(1, sizeof(orc_hier));
@@ -897,6 +904,7 @@ double orc_vcycle_loss(orc_hier* h, const double* r0, int m) {
 }
 
 double orc_vcycle_loss_grad(orc_hier* h, const double* r0, int m, double* const* domega) {
+  if (h->p.relax_type != 4 || h->p.cycle != 0) return NAN;  /* dD/domega = 1 / l1 below */
   int n = h->A[0].n;
   double** rs = (double**)xcalloc((size_t)m + 1, sizeof(double*));
   double* z = (double*)xcalloc((size_t)n, sizeof(double));

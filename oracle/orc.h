@@ -36,6 +36,8 @@ typedef struct orc_params {
   int true_res_every;  /* mixed precision: replace r by b - A u every k iterations (50) */
   int num_parts;       /* decoupled aggregation (Sec. 4.1): matching inside np row blocks (1) */
   int cycle;           /* Listing 1 cycle_type: 0 V-cycle, 2 W-cycle (0) */
+  int relax_type;      /* Listing 1 relax_type: 4 l1-Jacobi M_ii = sum_j |a_ij| (4), 0 Jacobi M_ii = a_ii;
+                          the same relaxation on the coarsest level */
 } orc_params;
 
 typedef struct orc_hier orc_hier;
@@ -73,7 +75,8 @@ int orc_fcg(orc_hier* h, const double* b, double* u, double tol, int maxit, int 
 void orc_spmv(const orc_hier* h, int k, const double* x, double* y);
 
 /* learned smoother: loss (1/m) ln(|r_m|/|r_0|), r_{t+1} = r_t - A B r_t, and its
- * gradient with respect to every per-row damping omega of every level */
+ * gradient with respect to every per-row damping omega of every level (l1-Jacobi
+ * V-cycle only: NaN for another relaxation or cycle) */
 double orc_vcycle_loss(orc_hier* h, const double* r0, int m);
 double orc_vcycle_loss_grad(orc_hier* h, const double* r0, int m, double* const* domega);
 

@@ -37,7 +37,7 @@ class amg_csr(ctypes.Structure):
 
 
 PARAM_FIELDS = ("aggr_steps", "max_levels", "coarse_size", "pre_sweeps", "post_sweeps", "coarse_sweeps",
-                "precision", "true_res_every", "use_graph", "graph_batch", "num_parts", "cycle")
+                "precision", "true_res_every", "use_graph", "graph_batch", "num_parts", "cycle", "relax_type")
 
 
 class amg_params(ctypes.Structure):

@@ -24,6 +24,7 @@ extern "C" void amg_params_default(amg_params* p) {
   p->graph_batch = 4;
   p->num_parts = 1;
   p->cycle = 0;
+  p->relax_type = 4;
 }
 
 extern "C" amg_status amg_info(const amg_handle* h, amg_info_t* info) {

@@ -548,6 +548,7 @@ extern "C" amg_status amg_vcycle_backward(amg_handle* h, const double* r, const 
   for (int k = 0; k < h->nl; ++k)
     if (!domega[k]) return amg_fail(h, AMG_ERR_INVALID_ARG, "domega[%d] is NULL", k);
   if (h->p.cycle != 0) return amg_fail(h, AMG_ERR_INVALID_ARG, "the adjoint covers the V-cycle only");
+  if (h->p.relax_type != 4) return amg_fail(h, AMG_ERR_INVALID_ARG, "the adjoint covers l1-Jacobi only");
   amg_status st = adj_prepare(h);
   if (st != AMG_OK) return st;
   cudaStream_t s = h->stream;

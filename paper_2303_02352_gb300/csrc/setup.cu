@@ -492,16 +492,20 @@ __global__ void k_bandwidth(int n, const int32_t* __restrict__ rp, const int32_t
 }
 
 // l1-Jacobi: M_ii = sum_j |a_ij| (CSR order), D_i = omega_i / M_ii
-__global__ void k_l1(int n, const int32_t* __restrict__ rp, const double* __restrict__ v,
-                     const double* __restrict__ omega, double* __restrict__ l1, double* __restrict__ dinv,
-                     float* __restrict__ dinvf) {
+// (jacobi: D_i = omega_i / a_ii, Listing 1 relax_type 0; the l1 norms are kept)
+__global__ void k_l1(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                     const double* __restrict__ v, const double* __restrict__ omega, double* __restrict__ l1,
+                     double* __restrict__ dinv, float* __restrict__ dinvf, int jacobi) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double s = 0.0;
-  for (int p = rp[i]; p < rp[i + 1]; ++p) s += fabs(v[p]);
+  double s = 0.0, a = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    s += fabs(v[p]);
+    if (ci[p] == i) a = v[p];
+  }
   l1[i] = s;
   double om = omega ? omega[i] : 1.0;
-  double d = om / s;
+  double d = om / (jacobi ? a : s);
   dinv[i] = d;
   if (dinvf) dinvf[i] = __double2float_rn(d);
 }
@@ -647,7 +651,8 @@ static amg_status build_members(amg_handle* h, Level& L, int nc) {
 
 amg_status amg_level_diag(amg_handle* h, int k) {
   Level& L = h->L[k];
-  k_l1<<<amg_blocks(L.n), AMG_BLOCK, 0, h->stream>>>(L.n, L.rp, L.v, L.omega, L.l1, L.dinv, L.dinvf);
+  k_l1<<<amg_blocks(L.n), AMG_BLOCK, 0, h->stream>>>(L.n, L.rp, L.ci, L.v, L.omega, L.l1, L.dinv, L.dinvf,
+                                                      h->p.relax_type == 0 ? 1 : 0);
   AMG_CK(h, cudaGetLastError());
   return AMG_OK;
 }
@@ -677,6 +682,8 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
   AMG_CK(h, cudaStreamSynchronize(s));
   if (ends[0] != 0 || ends[1] != nnz)
     return amg_fail(h, AMG_ERR_INVALID_ARG, "row_ptr[0] must be 0 and row_ptr[n] must equal nnz");
+  if (h->p.relax_type != 0 && h->p.relax_type != 4)
+    return amg_fail(h, AMG_ERR_INVALID_ARG, "relax_type must be 4 (l1-Jacobi) or 0 (Jacobi)");
   {
     int32_t* diagpos;
     AMG_ALLOC(h, diagpos, int32_t, n);

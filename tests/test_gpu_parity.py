@@ -404,6 +404,31 @@ def test_automatic_kernel_forms(big):
     assert f["stage_scale"][0] == 1
 
 
+@pytest.mark.parametrize("name", ["poisson16", "poisson13", "diff7_20", "diff27_12"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_jacobi_relaxation_parity(name, prec):
+    """Listing 1 relax_type 0 (D = 1 / a_ii) against the oracle: V-cycle and
+    solve; l1 norms unchanged."""
+    A = PROBLEMS[name]()
+    g, o = G(A, precision=prec, relax_type=0), O.Hierarchy(A, precision=prec, relax_type=0)
+    r = W.random_vector(A.n, 14)
+    tol = 1e-12 if prec == 0 else 1e-4
+    assert rel(g.vcycle(r).cpu().numpy(), o.vcycle(r)) < tol
+    assert np.array_equal(g.l1(0), o.level_l1(0))
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 15))
+    rg, ro = g.pcg_solve(b), o.fcg(b)
+    assert rg["status"] == ro["status"]
+    if ro["status"] == 0:
+        assert abs(rg["iters"] - ro["iters"]) <= (1 if prec == 0 else 2)
+        assert rg["true_rel_res"] < 1e-6
+
+
+def test_invalid_relax_type_rejected():
+    from paper_2303_02352_gb300 import amg
+    with pytest.raises(amg.AmgError):
+        G(W.poisson7(8), relax_type=1)
+
+
 PAIR_PROBLEMS = {
     "poisson32": lambda: W.poisson7(32),
     "poisson64": lambda: W.poisson7(64),

@@ -264,12 +264,13 @@ def dense_B(h, n):
     return np.stack([h.vcycle(e) for e in np.eye(n)], axis=1)
 
 
-def error_propagation(h, k, pre, post, coarse):
-    """I - B_k A_k = S^post (I - P B_{k+1} P^T A_k) S^pre, S = I - D A, written densely."""
+def error_propagation(h, k, pre, post, coarse, jacobi=False):
+    """I - B_k A_k = S^post (I - P B_{k+1} P^T A_k) S^pre, S = I - D A, written densely
+    (D = 1 / sum_j |a_ij|, or 1 / a_ii for Jacobi)."""
     rp, ci, v = h.level_csr(k)
     n = h.level_n(k)
     A = dense(rp, ci, v, n)
-    D = np.diag(1.0 / np.abs(A).sum(axis=1))
+    D = np.diag(1.0 / (np.diag(A) if jacobi else np.abs(A).sum(axis=1)))
     S = np.eye(n) - D @ A
     if k == h.num_levels - 1:
         return np.linalg.matrix_power(S, coarse) if coarse >= 0 else np.zeros((n, n))
@@ -278,7 +279,7 @@ def error_propagation(h, k, pre, post, coarse):
     P = prolongator(agg, nc).toarray()
     rpc, cic, vc = h.level_csr(k + 1)
     Ac = dense(rpc, cic, vc, nc)
-    Ec = error_propagation(h, k + 1, pre, post, coarse)
+    Ec = error_propagation(h, k + 1, pre, post, coarse, jacobi)
     Bc = (np.eye(nc) - Ec) @ np.linalg.inv(Ac)
     return np.linalg.matrix_power(S, post) @ (np.eye(n) - P @ Bc @ P.T @ A) @ np.linalg.matrix_power(S, pre)
 
@@ -294,6 +295,26 @@ def test_vcycle_equals_error_propagation_formula(gen):
     assert np.allclose(np.eye(A.n) - B @ Ad, E, atol=1e-12)
     assert np.allclose(B, B.T, atol=1e-13)
     np.linalg.cholesky(B)
+
+
+@pytest.mark.parametrize("gen", ["poisson", "diffusion"])
+def test_jacobi_relaxation_vcycle_equals_error_propagation_formula(gen):
+    """Listing 1 relax_type 0: D = 1 / a_ii on every level (the l1 norms stay
+    the row sums of |a_ij|)."""
+    A = W.poisson7(5) if gen == "poisson" else W.diffusion7(5, 2.0, 11)
+    h = O.Hierarchy(A, coarse_size=8, aggr_steps=2, relax_type=0)
+    B = dense_B(h, A.n)
+    Ad = A.to_scipy().toarray()
+    E = error_propagation(h, 0, 4, 4, 20, jacobi=True)
+    assert np.allclose(np.eye(A.n) - B @ Ad, E, atol=1e-12)
+    assert np.allclose(B, B.T, atol=1e-13)
+    # the two relaxations differ (on a 7-point Poisson row M_ii is 6 vs 12)
+    h4 = O.Hierarchy(A, coarse_size=8, aggr_steps=2)
+    assert not np.allclose(B, dense_B(h4, A.n))
+    assert np.allclose(h.level_l1(0), h4.level_l1(0))
+    # the oracle accepts only the two relaxations it implements
+    with pytest.raises(ValueError):
+        O.Hierarchy(A, relax_type=1)
 
 
 def test_vcycle_exact_coarse_spectrum_in_unit_interval():
