@@ -62,7 +62,7 @@ def load(path: str | None = None):
     global _LIB
     if _LIB is not None:
         return _LIB
-    path = path or SO_PATH
+    path = path or os.environ.get("AMG_LIB") or SO_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"libamg.so not found at {path}: build it with paper_2303_02352_gb300.build.build()")
     lib = ctypes.CDLL(path)

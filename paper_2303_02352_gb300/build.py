@@ -2,6 +2,9 @@
 
 Each .cu file under csrc/ is compiled in parallel to an object, then the
 objects are linked into _build/libamg.so.  Rebuilds only what changed.
+`build(checked=True)` makes the bounds-checked variant (AMG_CHECKED: every
+gather of the solve-phase kernels checks its index and raises a device flag
+instead of reading out of range) in _build/checked/libamg.so.
 """
 from __future__ import annotations
 
@@ -27,8 +30,8 @@ def _headers_mtime() -> float:
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, extra: list[str], bdir: str = BUILD) -> str:
+    obj = os.path.join(bdir, os.path.basename(src) + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _headers_mtime()):
         return obj
     tmp = obj + f".{os.getpid()}.tmp"
@@ -40,23 +43,25 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra: list[str] | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, extra: list[str] | None = None, checked: bool = False) -> str:
+    bdir = os.path.join(BUILD, "checked") if checked else BUILD
+    so = os.path.join(bdir, "libamg.so")
+    os.makedirs(bdir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    extra = list(extra or [])
+    extra = list(extra or []) + (["-DAMG_CHECKED"] if checked else [])
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    if os.path.exists(SO) and os.path.getmtime(SO) >= max(os.path.getmtime(o) for o in objs):
-        return SO
-    tmp = SO + f".{os.getpid()}.tmp"
+        objs = list(ex.map(lambda s: _compile(s, extra, bdir), srcs))
+    if os.path.exists(so) and os.path.getmtime(so) >= max(os.path.getmtime(o) for o in objs):
+        return so
+    tmp = so + f".{os.getpid()}.tmp"
     cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, SO)
+    os.replace(tmp, so)
     if verbose:
-        print("built", SO)
-    return SO
+        print("built", so)
+    return so
 
 
 if __name__ == "__main__":

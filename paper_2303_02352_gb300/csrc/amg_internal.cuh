@@ -29,6 +29,23 @@ struct DBuf {
 enum { ST_TIMEOUT = 1, ST_BADPTR = 2, ST_BADCOL = 4, ST_NODIAG = 8, ST_NOTPOS = 16, ST_NAN = 32,
        ST_ASYM = 64 };
 
+// Bounds-checked builds (AMG_CHECKED): every gather index of the solve-phase
+// kernels goes through amg_chk, which raises g_amg_bounds and substitutes
+// index 0 for an index outside [0, n); the host reports it as AMG_ERR_CUDA.
+// In normal builds amg_chk is the identity.
+#ifdef AMG_CHECKED
+static __device__ int g_amg_bounds = 0;  // one per translation unit; the solve-phase kernels live in solve.cu
+#endif
+__device__ __forceinline__ int amg_chk(int j, int n) {
+#ifdef AMG_CHECKED
+  if ((unsigned)j >= (unsigned)n) {
+    atomicOr(&g_amg_bounds, 1);
+    return 0;
+  }
+#endif
+  return j;
+}
+
 // FCG state kept on the device (Alg. 1 scalars and the stop logic)
 struct FcgState {
   int it;         // number of updates of u so far

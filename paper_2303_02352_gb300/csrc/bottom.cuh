@@ -93,6 +93,7 @@ __device__ __forceinline__ void rows(const BotLevel& L, const Ctx& c, int& r0, i
 // entry j of the distributed vector whose sections start at byte offset off
 template <typename T>
 __device__ __forceinline__ T dget(const BotLevel& L, const Ctx& c, int off, int j) {
+  j = amg_chk(j, L.n);
   const int o = (int)(((unsigned long long)(unsigned)j * L.magic) >> 32);
   const int k = j - o * L.chunk;
   const T* local = sec<T>(c, off);

@@ -269,10 +269,10 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pair(const PairArg
       VT s = 0;
       if (phase == 0) {
 #pragma unroll 8
-        for (int qq = q0; qq < q1; qq += TPR) s += (VT)to_acc(T.v[qq - av]) * __ldg(&a.z0[T.c[qq - ac]]);
+        for (int qq = q0; qq < q1; qq += TPR) s += (VT)to_acc(T.v[qq - av]) * __ldg(&a.z0[amg_chk(T.c[qq - ac], n)]);
       } else {
 #pragma unroll 8
-        for (int qq = q0; qq < q1; qq += TPR) s += (VT)to_acc(T.v[qq - av]) * __ldcg(&a.z1[T.c[qq - ac]]);
+        for (int qq = q0; qq < q1; qq += TPR) s += (VT)to_acc(T.v[qq - av]) * __ldcg(&a.z1[amg_chk(T.c[qq - ac], n)]);
       }
       if constexpr (TPR > 1) s = group_sum<TPR>(s);
       __syncwarp();

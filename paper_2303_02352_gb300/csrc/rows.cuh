@@ -120,6 +120,7 @@ struct RowArgs {
   const int32_t* mem;
   void* zf;
   int zf64;  // the finer iterate is double (else float)
+  int nf;    // rows of the finer level (bounds-checked builds)
 };
 
 // z_f[i] += z for the members i of aggregate `row`, in the finer level's
@@ -127,13 +128,13 @@ struct RowArgs {
 // members sub, sub + TPR, ...); each lane loads up to 8 member ids, then their
 // z_f entries, then stores, so one row costs three dependent round trips.
 template <typename FT, typename OT>
-__device__ __forceinline__ void prolong_chunk(FT* zf, const int32_t* mem, int base, int m1, int step, OT z) {
+__device__ __forceinline__ void prolong_chunk(FT* zf, const int32_t* mem, int base, int m1, int step, OT z, int nf) {
   int idx[8];
   FT v[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int m = base + u * step;
-    idx[u] = m < m1 ? __ldg(&mem[m]) : -1;
+    idx[u] = m < m1 ? amg_chk(__ldg(&mem[m]), nf) : -1;
   }
 #pragma unroll
   for (int u = 0; u < 8; ++u)
@@ -147,8 +148,8 @@ template <int TPR, typename MT, typename VT, typename OT>
 __device__ __forceinline__ void prolong_members(const RowArgs<MT, VT, OT>& a, int row, int sub, OT z) {
   const int m1 = __ldg(&a.mptr[row + 1]);
   for (int base = __ldg(&a.mptr[row]) + sub; base < m1; base += 8 * TPR) {
-    if (a.zf64) prolong_chunk(static_cast<double*>(a.zf), a.mem, base, m1, TPR, z);
-    else prolong_chunk(static_cast<float*>(a.zf), a.mem, base, m1, TPR, z);
+    if (a.zf64) prolong_chunk(static_cast<double*>(a.zf), a.mem, base, m1, TPR, z, a.nf);
+    else prolong_chunk(static_cast<float*>(a.zf), a.mem, base, m1, TPR, z, a.nf);
   }
 }
 
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
       const PipeTile<MT, SB>& T = P->st[stage];
       VT s = 0;
 #pragma unroll 8
-      for (int q = q0; q < q1; q += TPR) s += (VT)to_acc(T.v[q - av]) * __ldg(&a.x[T.c[q - ac]]);
+      for (int q = q0; q < q1; q += TPR) s += (VT)to_acc(T.v[q - av]) * __ldg(&a.x[amg_chk(T.c[q - ac], n)]);
       if constexpr (TPR > 1) s = group_sum<TPR>(s);
       __syncwarp();
       if (lane == 0) mbar_arrive(&P->empty[stage]);  // this warp is done with the stage

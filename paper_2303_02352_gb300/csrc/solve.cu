@@ -42,7 +42,7 @@ struct TileSmem {
 template <int R, typename MT, typename XT, typename AT>
 __device__ __forceinline__ AT tile_row_dot(TileSmem<MT>& sm, int row0, int row1, const int32_t* __restrict__ rp,
                                            const int32_t* __restrict__ ci, const MT* __restrict__ v,
-                                           const XT* __restrict__ x) {
+                                           const XT* __restrict__ x, int n) {
   constexpr int VE = TileSmem<MT>::VE, CAP = TileSmem<MT>::CAP;
   const int p0 = __ldg(&rp[row0]);
   const int p1 = __ldg(&rp[row1]);
@@ -66,10 +66,10 @@ __device__ __forceinline__ AT tile_row_dot(TileSmem<MT>& sm, int row0, int row1,
     for (int k = threadIdx.x; k < nc; k += R) dc[k] = __ldg(gc + k);
     __syncthreads();
 #pragma unroll 8
-    for (int q = q0; q < q1; ++q) s += (AT)to_acc(sm.v[q - a0]) * (AT)__ldg(&x[sm.c[q - c0]]);
+    for (int q = q0; q < q1; ++q) s += (AT)to_acc(sm.v[q - a0]) * (AT)__ldg(&x[amg_chk(sm.c[q - c0], n)]);
   } else {
 #pragma unroll 4
-    for (int q = q0; q < q1; ++q) s += (AT)to_acc(__ldg(&v[q])) * (AT)__ldg(&x[__ldg(&ci[q])]);
+    for (int q = q0; q < q1; ++q) s += (AT)to_acc(__ldg(&v[q])) * (AT)__ldg(&x[amg_chk(__ldg(&ci[q]), n)]);
   }
   return s;
 }
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(R) k_sweep(int n, const int32_t* __restrict__ 
   if (*skip) return;
   __shared__ __align__(16) TileSmem<MT> sm;
   const int row0 = blockIdx.x * R, row1 = min(row0 + R, n);
-  const VT s = tile_row_dot<R, MT, VT, VT>(sm, row0, row1, rp, ci, v, z);
+  const VT s = tile_row_dot<R, MT, VT, VT>(sm, row0, row1, rp, ci, v, z, n);
   const int row = row0 + threadIdx.x;
   if (row < row1) zout[row] = (OT)(z[row] + dinv[row] * (r[row] - s));
 }
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(R) k_resid(int n, const int32_t* __restrict__ 
   if (*skip) return;
   __shared__ __align__(16) TileSmem<MT> sm;
   const int row0 = blockIdx.x * R, row1 = min(row0 + R, n);
-  const VT s = tile_row_dot<R, MT, VT, VT>(sm, row0, row1, rp, ci, v, z);
+  const VT s = tile_row_dot<R, MT, VT, VT>(sm, row0, row1, rp, ci, v, z, n);
   const int row = row0 + threadIdx.x;
   if (row < row1) tout[row] = r[row] - s;
 }
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(R) k_spmv(int n, const int32_t* __restrict__ r
                                             double* __restrict__ y) {
   __shared__ __align__(16) TileSmem<double> sm;
   const int row0 = blockIdx.x * R, row1 = min(row0 + R, n);
-  const double s = tile_row_dot<R, double, double, double>(sm, row0, row1, rp, ci, v, x);
+  const double s = tile_row_dot<R, double, double, double>(sm, row0, row1, rp, ci, v, x, n);
   const int row = row0 + threadIdx.x;
   if (row < row1) y[row] = s;
 }
@@ -155,14 +155,15 @@ __global__ void __launch_bounds__(R) k_spmv(int n, const int32_t* __restrict__ r
 // more rows per thread would only serialise them)
 template <typename VT, typename CT>
 __global__ void __launch_bounds__(AMG_BLOCK) k_restrict(int nc, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
-                                                        const VT* __restrict__ t, CT* __restrict__ rc, const int* skip) {
+                                                        const VT* __restrict__ t, CT* __restrict__ rc, const int* skip,
+                                                        int n) {
   pdl_trigger();
   pdl_wait();
   if (*skip) return;
   const int J = blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= nc) return;
   VT s = 0;
-  for (int m = mptr[J]; m < mptr[J + 1]; ++m) s += t[mem[m]];
+  for (int m = mptr[J]; m < mptr[J + 1]; ++m) s += t[amg_chk(mem[m], n)];
   rc[J] = (CT)s;
 }
 
@@ -173,14 +174,14 @@ template <typename VT, typename CT>
 __global__ void __launch_bounds__(AMG_BLOCK) k_restrict_first(int nc, const int32_t* __restrict__ mptr,
                                                               const int32_t* __restrict__ mem, const VT* __restrict__ t,
                                                               const CT* __restrict__ dinv_c, CT* __restrict__ rc,
-                                                              CT* __restrict__ zc, const int* skip) {
+                                                              CT* __restrict__ zc, const int* skip, int n) {
   pdl_trigger();
   pdl_wait();
   if (*skip) return;
   const int J = blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= nc) return;
   VT s = 0;
-  for (int m = mptr[J]; m < mptr[J + 1]; ++m) s += t[mem[m]];
+  for (int m = mptr[J]; m < mptr[J + 1]; ++m) s += t[amg_chk(mem[m], n)];
   const CT r = (CT)s;
   rc[J] = r;
   zc[J] = dinv_c[J] * r;
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(AMG_BLOCK) k_restrict_first(int nc, const int3
 // z_i += z_c[agg(i)]  (unit piecewise-constant prolongator)
 template <typename VT, typename CT>
 __global__ void __launch_bounds__(AMG_BLOCK) k_prolong(int n, const int32_t* __restrict__ agg, const CT* __restrict__ zc,
-                                                       VT* __restrict__ z, const int* skip) {
+                                                       VT* __restrict__ z, const int* skip, int nc) {
   pdl_trigger();
   pdl_wait();
   if (*skip) return;
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(AMG_BLOCK) k_prolong(int n, const int32_t* __r
 #pragma unroll
   for (int u = 0; u < EW; ++u) {
     const int i = i0 + u * T;
-    if (i < n) z[i] = zz[u] + (VT)zc[a[u]];
+    if (i < n) z[i] = zz[u] + (VT)zc[amg_chk(a[u], nc)];
   }
 }
 
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(R) k_fcg_resid(int n, const int32_t* __restric
   const int ntiles = (n + R - 1) / R;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int row0 = tile * R, row1 = min(row0 + R, n);
-    const double s = tile_row_dot<R, double, double, double>(sm, row0, row1, rp, ci, v, u);
+    const double s = tile_row_dot<R, double, double, double>(sm, row0, row1, rp, ci, v, u, n);
     const int row = row0 + threadIdx.x;
     if (row < row1) {
       const double bi = b[row], ri = bi - s;
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(R) k_fcg_spmv_dots(int n, const int32_t* __res
   const int ntiles = (n + R - 1) / R;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int row0 = tile * R, row1 = min(row0 + R, n);
-    const double s = tile_row_dot<R, double, double, double>(sm, row0, row1, rp, ci, v, w);
+    const double s = tile_row_dot<R, double, double, double>(sm, row0, row1, rp, ci, v, w, n);
     const int row = row0 + threadIdx.x;
     if (row < row1) {
       const double wi = w[row];
@@ -549,7 +550,7 @@ static bool launch_sweep_prolong(cudaStream_t s, const Level& C, const MT* vals,
   const int tiles = (C.n + C.R - 1) / C.R;
   if (!any_size && rows_grid<PM_SWEEP_PROLONG, MT, VT, VT>(C.R, C.sb, C.n) < tiles) return false;
   RowArgs<MT, VT, VT> a{C.n, C.rp, C.ci, vals, z, dinv, r, nullptr, nullptr, out, skip, nullptr, nullptr, nullptr, flags,
-                        F.mptr, F.mem, zf, F.lowp ? 0 : 1};
+                        F.mptr, F.mem, zf, F.lowp ? 0 : 1, F.n};
   launch_rows<PM_SWEEP_PROLONG>(s, C.R, C.sb, a);
   return true;
 }
@@ -908,15 +909,15 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
   if (k + 1 == h->kb) {  // the bottom levels in one launch
     const double sc = vec_bytes(C);
     if (k + 1 == h->nl - 1) {
-      amg_launch(k_restrict<VT, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (double*)C.r, R.skip);
+      amg_launch(k_restrict<VT, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (double*)C.r, R.skip, L.n);
       R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 8.0 * nc);
       rec_bottom(R);
-      amg_launch(k_prolong<VT, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, (const double*)C.za, z, R.skip);
+      amg_launch(k_prolong<VT, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, (const double*)C.za, z, R.skip, C.n);
     } else {
-      amg_launch(k_restrict<VT, VT>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip);
+      amg_launch(k_restrict<VT, VT>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip, L.n);
       R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc);
       rec_bottom(R);
-      amg_launch(k_prolong<VT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, (const VT*)C.za, z, R.skip);
+      amg_launch(k_prolong<VT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, (const VT*)C.za, z, R.skip, C.n);
     }
     R.add(4.0 * n + sc * nc + 2.0 * sx * n);
     return;
@@ -930,10 +931,10 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
     const bool fr = fuse && h->p.coarse_sweeps > 0;
     if (fr) {
       amg_launch(k_restrict_first<VT, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t,
-                 (const double*)C.dinv, (double*)C.r, (double*)C.za, R.skip);
+                 (const double*)C.dinv, (double*)C.r, (double*)C.za, R.skip, L.n);
       R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 24.0 * nc);
     } else {
-      amg_launch(k_restrict<VT, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (double*)C.r, R.skip);
+      amg_launch(k_restrict<VT, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (double*)C.r, R.skip, L.n);
       R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 8.0 * nc);
     }
     double* zc = rec_coarse(R, k + 1, (const double*)C.r, nullptr, fr, fuse ? &pro : nullptr);
@@ -950,7 +951,7 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
       zc = e;
     }
     if (!pro.done) {
-      amg_launch(k_prolong<VT, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip);
+      amg_launch(k_prolong<VT, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip, C.n);
       R.add(4.0 * n + 8.0 * nc + 2.0 * sx * n);
     }
   } else {
@@ -959,10 +960,10 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
     if (fr) {
       const VT* dc = C.lowp ? (const VT*)C.dinvf : (const VT*)C.dinv;
       amg_launch(k_restrict_first<VT, VT>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, dc,
-                 (VT*)C.r, (VT*)C.za, R.skip);
+                 (VT*)C.r, (VT*)C.za, R.skip, L.n);
       R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 3.0 * sc * nc);
     } else {
-      amg_launch(k_restrict<VT, VT>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip);
+      amg_launch(k_restrict<VT, VT>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip, L.n);
       R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc);
     }
     Prol* pp = fuse ? &pro : nullptr;
@@ -987,7 +988,7 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
       zc = e;
     }
     if (!pro.done) {
-      amg_launch(k_prolong<VT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip);
+      amg_launch(k_prolong<VT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip, C.n);
       R.add(4.0 * n + sc * nc + 2.0 * sx * n);
     }
   }
@@ -1295,11 +1296,24 @@ extern "C" amg_status amg_check_bounded_wait(int32_t limit_us, void* stream) {
   return (host & ST_TIMEOUT) ? AMG_ERR_TIMEOUT : AMG_OK;
 }
 
+#ifdef AMG_CHECKED
+// read and clear the bounds flag of this translation unit's kernels
+static int take_bounds_flag() {
+  int b = 0, z = 0;
+  cudaMemcpyFromSymbol(&b, g_amg_bounds, sizeof(int));
+  if (b) cudaMemcpyToSymbol(g_amg_bounds, &z, sizeof(int));
+  return b;
+}
+#endif
+
 // error bits raised by bounded device waits during the solve phase
 static amg_status check_device_flags(amg_handle* h) {
   int f = 0;
   AMG_CK(h, cudaMemcpyAsync(&f, h->dev_flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   AMG_CK(h, cudaStreamSynchronize(h->stream));
+#ifdef AMG_CHECKED
+  if (take_bounds_flag()) return amg_fail(h, AMG_ERR_CUDA, "bounds check: a gather index was out of range");
+#endif
   if (!f) return AMG_OK;
   AMG_CK(h, cudaMemsetAsync(h->dev_flags, 0, sizeof(int), h->stream));
   if (f & ST_TIMEOUT) {
@@ -1493,13 +1507,13 @@ static amg_status launch_one(amg_handle* h, int which, int k) {
       Level& C = h->L[k + 1];
       bool ccoarse = (k + 1 == h->nl - 1);
       if (which == 2) {
-        if (!L.lowp) amg_launch(k_restrict<double, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (double*)L.t, (double*)C.r, skip);
-        else if (ccoarse) amg_launch(k_restrict<float, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (float*)L.t, (double*)C.r, skip);
-        else amg_launch(k_restrict<float, float>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (float*)L.t, (float*)C.r, skip);
+        if (!L.lowp) amg_launch(k_restrict<double, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (double*)L.t, (double*)C.r, skip, L.n);
+        else if (ccoarse) amg_launch(k_restrict<float, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (float*)L.t, (double*)C.r, skip, L.n);
+        else amg_launch(k_restrict<float, float>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (float*)L.t, (float*)C.r, skip, L.n);
       } else {
-        if (!L.lowp) amg_launch(k_prolong<double, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (double*)C.za, (double*)L.za, skip);
-        else if (ccoarse) amg_launch(k_prolong<float, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (double*)C.za, (float*)L.za, skip);
-        else amg_launch(k_prolong<float, float>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (float*)C.za, (float*)L.za, skip);
+        if (!L.lowp) amg_launch(k_prolong<double, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (double*)C.za, (double*)L.za, skip, C.n);
+        else if (ccoarse) amg_launch(k_prolong<float, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (double*)C.za, (float*)L.za, skip, C.n);
+        else amg_launch(k_prolong<float, float>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (float*)C.za, (float*)L.za, skip, C.n);
       }
       break;
     }
@@ -1511,16 +1525,16 @@ static amg_status launch_one(amg_handle* h, int which, int k) {
       if (which == 6) {
         if (ccoarse && !L.lowp)
           amg_launch(k_restrict_first<double, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem,
-                     (const double*)L.t, (const double*)C.dinv, (double*)C.r, (double*)C.za, skip);
+                     (const double*)L.t, (const double*)C.dinv, (double*)C.r, (double*)C.za, skip, L.n);
         else if (ccoarse)
           amg_launch(k_restrict_first<float, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem,
-                     (const float*)L.t, (const double*)C.dinv, (double*)C.r, (double*)C.za, skip);
+                     (const float*)L.t, (const double*)C.dinv, (double*)C.r, (double*)C.za, skip, L.n);
         else if (!L.lowp)
           amg_launch(k_restrict_first<double, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem,
-                     (const double*)L.t, (const double*)C.dinv, (double*)C.r, (double*)C.za, skip);
+                     (const double*)L.t, (const double*)C.dinv, (double*)C.r, (double*)C.za, skip, L.n);
         else
           amg_launch(k_restrict_first<float, float>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem,
-                     (const float*)L.t, (const float*)C.dinvf, (float*)C.r, (float*)C.za, skip);
+                     (const float*)L.t, (const float*)C.dinvf, (float*)C.r, (float*)C.za, skip, L.n);
       } else {
         bool ok;
         if (ccoarse || !C.lowp)
