@@ -514,6 +514,42 @@ def test_wcycle_parity(prec):
 
 
 @pytest.fixture(scope="module")
+def huge():
+    A = W.poisson7(320)
+    return A, G(A)
+
+
+def test_full_size_320_closed_form_hierarchy_and_solve(huge):
+    """The largest single-GPU configuration, 7-point Poisson 320^3 (32.8M rows),
+    checked by what holds at any size: level k is 4^k times the 7-point
+    Laplacian on (320 / 2^k)^3 (sizes, nonzeros and values in closed form),
+    level-0 aggregates are the 2x2x2 cubes numbered lexicographically (sampled
+    rows), B is symmetric, and the solve reaches the true FP64 1e-6."""
+    A, g = huge
+    inf = g.info()
+    ms = [320, 160, 80, 40, 20]
+    assert inf["n"] == [m ** 3 for m in ms]
+    assert inf["nnz"] == [7 * m ** 3 - 6 * m ** 2 for m in ms]
+    rng = np.random.default_rng(5)
+    rows = rng.integers(0, A.n, 200000)
+    agg = g.aggregates(0)
+    x, y, z = rows % 320, (rows // 320) % 320, rows // (320 * 320)
+    assert np.array_equal(agg[rows], x // 2 + 160 * (y // 2) + 160 * 160 * (z // 2))
+    rp, ci, v = g.level_csr(4)
+    ref = W.poisson7(20)
+    assert np.array_equal(rp, ref.row_ptr) and np.array_equal(ci, ref.col_idx)
+    assert np.array_equal(v, ref.val * 4.0 ** 4)
+    u1, u2 = W.random_vector(A.n, 31), W.random_vector(A.n, 32)
+    b1, b2 = g.vcycle(u1).cpu().numpy(), g.vcycle(u2).cpu().numpy()
+    assert abs(u1 @ b2 - b1 @ u2) < 1e-10 * abs(u1 @ b2)
+    xs = W.random_vector(A.n, 5)
+    res = g.pcg_solve(W.rhs_from_solution(A, xs))
+    assert res["status"] == 0 and res["true_rel_res"] < 1e-6 and 12 <= res["iters"] <= 14
+    err = np.linalg.norm(res["x"].cpu().numpy() - xs) / np.linalg.norm(xs)
+    assert err < 1e-3
+
+
+@pytest.fixture(scope="module")
 def big27():
     A, b, _ = W.config("diffusion27_128")
     return A, b, G(A)
