@@ -484,6 +484,15 @@ __global__ void k_maxrow(int n, const int32_t* __restrict__ rp, int* out) {
   if (i < n) atomicMax(out, rp[i + 1] - rp[i]);
 }
 
+// largest number of entries in a tile of R consecutive rows
+__global__ void k_tile_max(int n, const int32_t* __restrict__ rp, int R, int* out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r0 = t * R;
+  if (r0 >= n) return;
+  const int r1 = min(n, r0 + R);
+  atomicMax(out, rp[r1] - rp[r0]);
+}
+
 // bandwidth max |i - j| (columns are sorted: the first and last entry decide)
 __global__ void k_bandwidth(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int* out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -802,20 +811,37 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
     AMG_CK(h, cudaMemsetAsync(h->dev_flags, 0, sizeof(int), s));
     L.bw = bwd;
     const int vb = L.lowp ? ((h->p.precision == AMG_FP32_BF16FINE && k == 0) ? 2 : 4) : 8;
-    L.Rd = amg_tile_rows(mr, 8);
+    L.Rd = amg_tile_rows(mr, 8);   // non-pipelined kernels (their tile buffer falls back to direct loads)
     L.R = amg_tile_rows(mr, vb);
     const bool big = L.n >= h->small_rows;
-    // pipelined kernels: tile heights down to 8 rows (32 threads per row)
-    const int Rp = std::min(amg_tile_rows(mr, vb, PIPE_CONSUMERS / 32), PIPE_CONSUMERS / std::max(1, h->min_tpr));
-    const int Rpd = std::min(amg_tile_rows(mr, 8, PIPE_CONSUMERS / 32), PIPE_CONSUMERS / std::max(1, h->min_tpr));
-    L.piped = h->use_pipe && (int64_t)Rpd * mr <= amg_pipe_tile_bytes(8) / 12;
-    L.pipe = h->use_pipe && big && (int64_t)Rp * mr <= amg_pipe_tile_bytes(vb) / (vb + 4);
+    // pipelined kernels: the tallest tile (power of two, 8 .. 256 / min_tpr
+    // rows) whose tiles all fit a stage, from the largest number of entries of
+    // any tile of that height (rows of average length share a tile with the
+    // longest ones, so this beats sizing by the longest row)
+    int tmax[6];  // tile_max for R = 256 >> i
+    for (int i = 0; i < 6; ++i) {
+      k_tile_max<<<amg_blocks((L.n + (256 >> i) - 1) / (256 >> i)), AMG_BLOCK, 0, s>>>(L.n, L.rp, 256 >> i, h->dev_flags);
+      st0 = sync_read(h, h->dev_flags, &tmax[i]);
+      if (st0 != AMG_OK) return st0;
+      AMG_CK(h, cudaMemsetAsync(h->dev_flags, 0, sizeof(int), s));
+    }
+    const int rmax = PIPE_CONSUMERS / std::max(1, h->min_tpr);
+    auto fit = [&](int cap) {  // tallest fitting tile height, 0: none
+      for (int i = 0; i < 6; ++i)
+        if ((256 >> i) <= rmax && tmax[i] <= cap) return 256 >> i;
+      return 0;
+    };
+    const int cap8 = amg_pipe_tile_bytes(8) / 12;
+    const int Rp = fit(amg_pipe_tile_bytes(vb) / (vb + 4));
+    const int Rpd = fit(cap8);
+    L.piped = h->use_pipe && Rpd > 0;
+    L.pipe = h->use_pipe && big && Rp > 0;
     if (L.piped) L.Rd = Rpd;
     if (L.pipe) L.R = Rp;
     // FP64 values and rows too long for one thread per row in a normal stage:
-    // a 4x stage holds 256 rows of up to 32 entries (fewer FP64 instructions
-    // per row than several threads per row with a shuffle reduction; FP64
-    // issue limits these kernels on this part)
+    // a 4x stage takes 256-row tiles of up to 8192 entries (fewer FP64
+    // instructions per row than several threads per row with a shuffle
+    // reduction; FP64 issue limits these kernels on this part)
     // forms: 2 = 2x stages, 128 rows, 2 threads per row; 4 = 4x stages, 256
     // rows, one thread per row; 5 = two consumer groups, four 2x stages, 128
     // rows, one thread per row
@@ -823,8 +849,11 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
     const int rbig = sbig == 4 ? 256 : 128;                          // rows per tile
     const int scale = sbig == 4 ? 4 : 2;                             // stage scale
     const int tpr_big = sbig == 2 ? 2 : 1;
+    // (only on levels with at least one tile per multiprocessor: one block per
+    // multiprocessor runs this form, and smaller levels want more, shorter tiles)
     const bool big_rows = (sbig == 2 || sbig == 4 || sbig == 5) && h->min_tpr <= tpr_big &&
-                          (int64_t)rbig * mr <= (int64_t)amg_pipe_tile_bytes(8) * scale / 12;
+                          tmax[rbig == 256 ? 0 : 1] <= cap8 * scale &&
+                          (int64_t)(L.n + rbig - 1) / rbig >= (int64_t)amg_num_sms();
     if (L.pipe && vb == 8 && L.R < rbig && big_rows) {
       L.R = rbig;
       L.sb = sbig;

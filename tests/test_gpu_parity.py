@@ -389,18 +389,21 @@ def test_long_row_kernel_forms(form, name, monkeypatch):
 
 def test_automatic_kernel_forms(big):
     """The setup's automatic choices: one thread per row in 4x stages for the
-    27-point FP64 fine level, standard stages for 7-point, and the fused
+    27-point FP64 fine level (64^3), standard stages for 7-point, and the fused
     bottom for the regular 7-point 160^3 hierarchy (levels of 8,000 and 4,000
     rows) but not for the irregular 27-point one (owner-spread rule).  Small
     grids whose bottom levels are mostly boundary rows may decline it too."""
     p = big[1].info()
     assert p["tile_rows"][0] == 256 and p["stage_scale"][0] == 1
     assert p["bottom_level"] == 3 and p["num_levels"] == 5
-    d = G(W.diffusion27(32, 2.0, 3)).info()
+    d27 = W.diffusion27(64, 2.0, 3)
+    d = G(d27).info()
     assert d["tile_rows"][0] == 256 and d["stage_scale"][0] == 4
     assert d["bottom_level"] == d["num_levels"]
+    # levels with fewer 256-row tiles than multiprocessors keep standard stages
+    assert all(sc == 1 for n, sc in zip(d["n"], d["stage_scale"]) if n < 256 * 152)
     # low precision: the float fine level keeps standard stages
-    f = G(W.diffusion27(32, 2.0, 3), precision=1).info()
+    f = G(d27, precision=1).info()
     assert f["stage_scale"][0] == 1
 
 
