@@ -23,6 +23,7 @@ _LIB = None
 
 FP64, FP32, FP32_BF16FINE = 0, 1, 2
 COARSE_L1JACOBI, COARSE_DENSE_CHOL = 0, 1
+PROLONG_UNIT, PROLONG_W_NORMALIZED = 0, 1
 OK, NOT_CONVERGED, ERR_ARG, ERR_BREAKDOWN = 0, 1, -1, -3
 
 
@@ -43,7 +44,7 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int) for name in (
         "aggr_steps", "max_levels", "coarse_size", "pre_sweeps", "post_sweeps",
-        "coarse_sweeps", "coarse_solver", "precision", "true_res_every", "num_parts", "cycle", "relax_type")]
+        "coarse_sweeps", "coarse_solver", "precision", "true_res_every", "num_parts", "cycle", "relax_type", "prolong_scale")]
 
 
 def _lib():
@@ -147,6 +148,7 @@ class Params:
     num_parts: int = 1
     cycle: int = 0
     relax_type: int = 4
+    prolong_scale: int = PROLONG_UNIT  # PROLONG_W_NORMALIZED: ablation of the prolongator values
 
     def _c(self):
         p = _Params()

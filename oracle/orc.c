@@ -52,6 +52,7 @@ struct orc_hier {
   double* l1[ORC_MAXL];    /* l1 row norms */
   double* omega[ORC_MAXL]; /* per-row damping, 1 by default */
   double* dinv[ORC_MAXL];  /* omega / l1 */
+  double* wsv[ORC_MAXL];   /* smooth vector w^k of the w-normalised prolongators (NULL for unit P) */
   float* fval[ORC_MAXL];   /* mixed precision: rounded level values */
   float* fdinv[ORC_MAXL];
   double* chol;            /* dense Cholesky factor of the coarsest matrix (pins only) */
@@ -72,6 +73,7 @@ void orc_params_default(orc_params* p) {
   p->num_parts = 1;
   p->cycle = 0;
   p->relax_type = 4;     /* Listing 1: relax_type 4 (l1-Jacobi) */
+  p->prolong_scale = ORC_PROLONG_UNIT;
 }
 
 static void* xcalloc(size_t n, size_t s) {
@@ -321,17 +323,29 @@ static void csr_free(ocsr* a) {
 }
 
 /* l1 row norms and D = omega / M with M_ii = sum_j |a_ij| (l1-Jacobi) or
- * M_ii = a_ii (Jacobi, Listing 1 relax_type 0) */
+ * M_ii = a_ii (Jacobi, Listing 1 relax_type 0).
+ *
+ * w-normalised prolongators (Sec. 3.1: P's entries come from the smooth vector,
+ * w^{k+1} = R w^k): P^k_{i,I} = w^k_i / |w^k restricted to I|, so
+ * w^{k+1}_I = |w^k on I|_2 and, by induction from w^0 = 1, the normalised
+ * level matrix is W_k^{-1} A^k W_k^{-1} (W_k = diag(w^k)) with A^k the
+ * unit-prolongator matrix kept here.  Residuals, corrections and the error
+ * propagation map into the unit coordinates through the same W_k, and there
+ * the only change is the smoother diagonal: l1-Jacobi on the normalised
+ * matrix becomes M_I = sum_J |a_IJ| w_I / w_J, while Jacobi (a_II) and the
+ * matching weights (invariant under the scaling) are unchanged. */
 static void level_diag(orc_hier* h, int k) {
   ocsr* A = &h->A[k];
+  const double* w = h->wsv[k];
   for (int i = 0; i < A->n; ++i) {
-    double s = 0.0, d = 0.0;
+    double s = 0.0, d = 0.0, m = 0.0;
     for (int32_t p = A->rp[i]; p < A->rp[i + 1]; ++p) {
       s += fabs(A->v[p]);
+      if (w) m += fabs(A->v[p]) * (w[i] / w[A->ci[p]]);
       if (A->ci[p] == i) d = A->v[p];
     }
     h->l1[k][i] = s;
-    h->dinv[k][i] = h->omega[k][i] / (h->p.relax_type == 0 ? d : s);
+    h->dinv[k][i] = h->omega[k][i] / (h->p.relax_type == 0 ? d : (w ? m : s));
   }
 }
 
@@ -375,6 +389,7 @@ static void build_chol(orc_hier* h) {
 orc_hier* orc_setup(int n, const int32_t* rp, const int32_t* ci, const double* v, const orc_params* p) {
   if (n <= 0 || !rp || !ci || !v || !p) return NULL;
   if (p->relax_type != 0 && p->relax_type != 4) return NULL;
+  if (p->prolong_scale != ORC_PROLONG_UNIT && p->prolong_scale != ORC_PROLONG_W_NORMALIZED) return NULL;
   for (int i = 0; i < n; ++i)
     if (find_diag(rp, ci, i) < 0) return NULL;
   orc_hier* h = (orc_hier*)xcalloc(1, sizeof(orc_hier));
@@ -449,6 +464,17 @@ orc_hier* orc_setup(int n, const int32_t* rp, const int32_t* ci, const double* v
   csr_free(&cur);
   free(bnd);
 
+  if (p->prolong_scale == ORC_PROLONG_W_NORMALIZED) {
+    /* w^0 = 1; w^{k+1}_I = sqrt(sum over i in I of (w^k_i)^2) */
+    h->wsv[0] = (double*)xcalloc((size_t)n, sizeof(double));
+    for (int i = 0; i < n; ++i) h->wsv[0][i] = 1.0;
+    for (int k = 0; k + 1 < h->nl; ++k) {
+      double* wc = (double*)xcalloc((size_t)h->A[k + 1].n, sizeof(double));
+      for (int i = 0; i < h->A[k].n; ++i) wc[h->agg[k][i]] += h->wsv[k][i] * h->wsv[k][i];
+      for (int c = 0; c < h->A[k + 1].n; ++c) wc[c] = sqrt(wc[c]);
+      h->wsv[k + 1] = wc;
+    }
+  }
   for (int k = 0; k < h->nl; ++k) {
     int nk = h->A[k].n;
     h->l1[k] = (double*)xcalloc((size_t)nk, sizeof(double));
@@ -468,6 +494,7 @@ void orc_free(orc_hier* h) {
     csr_free(&h->A[k]);
     free(h->agg[k]);
     free(h->l1[k]);
+    free(h->wsv[k]);
     free(h->omega[k]);
     free(h->dinv[k]);
     free(h->fval[k]);
@@ -904,7 +931,7 @@ double orc_vcycle_loss(orc_hier* h, const double* r0, int m) {
 }
 
 double orc_vcycle_loss_grad(orc_hier* h, const double* r0, int m, double* const* domega) {
-  if (h->p.relax_type != 4 || h->p.cycle != 0) return NAN;  /* dD/domega = 1 / l1 below */
+  if (h->p.relax_type != 4 || h->p.cycle != 0 || h->wsv[0]) return NAN; /* dD/domega = 1 / l1 below */
   int n = h->A[0].n;
   double** rs = (double**)xcalloc((size_t)m + 1, sizeof(double*));
   double* z = (double*)xcalloc((size_t)n, sizeof(double));

@@ -23,6 +23,7 @@ extern "C" {
 enum { ORC_OK = 0, ORC_NOT_CONVERGED = 1, ORC_ERR_ARG = -1, ORC_ERR_BREAKDOWN = -3 };
 enum { ORC_COARSE_L1JACOBI = 0, ORC_COARSE_DENSE_CHOL = 1 };
 enum { ORC_FP64 = 0, ORC_FP32 = 1, ORC_FP32_BF16FINE = 2 };
+enum { ORC_PROLONG_UNIT = 0, ORC_PROLONG_W_NORMALIZED = 1 };
 
 typedef struct orc_params {
   int aggr_steps;      /* s: pairwise steps merged per level (3 -> aggregates <= 8) */
@@ -38,6 +39,9 @@ typedef struct orc_params {
   int cycle;           /* Listing 1 cycle_type: 0 V-cycle, 2 W-cycle (0) */
   int relax_type;      /* Listing 1 relax_type: 4 l1-Jacobi M_ii = sum_j |a_ij| (4), 0 Jacobi M_ii = a_ii;
                           the same relaxation on the coarsest level */
+  int prolong_scale;   /* ORC_PROLONG_UNIT (P 1 = 1, the default) or ORC_PROLONG_W_NORMALIZED
+                          (entries w_i / |w_aggregate|, P^T P = I; ablation of the prolongator
+                          values of Sec. 3.1, oracle only) */
 } orc_params;
 
 typedef struct orc_hier orc_hier;

@@ -311,3 +311,22 @@ class Hierarchy:
         b = ctypes.c_double(0.0)
         self._check(self._lib.amg_kernel_bytes(self._h, which, level, ctypes.byref(b)))
         return b.value
+
+
+# -- module-level calls (the Python form of amg_setup / amg_pcg_solve) ------
+def setup(A, stream=None, **params) -> Hierarchy:
+    """amg_setup: build the hierarchy of ``A`` (a ``torch.sparse_csr_tensor``
+    of float64, on CUDA or host, or any object with ``n``, ``row_ptr``,
+    ``col_idx``, ``val``).  Keyword arguments override ``amg_params`` fields.
+    Raises AmgError when the setup fails."""
+    return Hierarchy(A, stream=stream, **params)
+
+
+def solve(h: Hierarchy, b, x0=None, tol=1e-6, maxit=1000):
+    """amg_pcg_solve: Alg. 1 preconditioned by the hierarchy's cycle.
+    Returns ``(x, iters, hist)``: the device solution (float64), the number
+    of iterations and the host array ||r_i|| / ||b|| for i = 0..iters.  A run that stops
+    at ``maxit`` without reaching ``tol`` still returns its iterate (status
+    AMG_NOT_CONVERGED, available from ``h.pcg_solve``)."""
+    out = h.pcg_solve(b, x0=x0, tol=tol, maxit=maxit)
+    return out["x"], out["iters"], out["hist"]

@@ -149,13 +149,11 @@ def _autograd():
     return MLPFn, VCycleFn, SpMVFn
 
 
-MLPFn = VCycleFn = SpMVFn = None
+MLPFn, VCycleFn, SpMVFn = _autograd()
 
 
 def _ensure():
-    global MLPFn, VCycleFn, SpMVFn
-    if MLPFn is None:
-        MLPFn, VCycleFn, SpMVFn = _autograd()
+    """Kept for callers of the earlier lazy form: the Functions exist at import."""
 
 
 def level_features(h):

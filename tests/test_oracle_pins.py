@@ -585,3 +585,93 @@ def test_wcycle_equals_error_propagation_formula():
     Ad = A.to_scipy().toarray()
     assert np.allclose(np.eye(A.n) - B @ Ad, ew(0), atol=1e-12)
     assert np.allclose(B, B.T, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------
+# prolongator values (Sec. 3.1: entries from the smooth vector, w^{k+1} = R w^k):
+# the w-normalised ablation against the literal dense construction
+
+
+def _normalised_hierarchy(A, h):
+    """Literal w-normalised hierarchy: P_{i,I} = w_i / |w on I|, w^{k+1} = P^T w^k,
+    A^{k+1} = P^T A^k P, from the level-0 matrix and the oracle's aggregates."""
+    Ak = A.to_scipy().toarray()
+    w = np.ones(A.n)
+    mats, Ps, ws = [Ak], [], [w]
+    for k in range(h.num_levels - 1):
+        agg = h.level_agg(k)
+        nc = h.level_n(k + 1)
+        norms = np.sqrt(np.bincount(agg, weights=w * w, minlength=nc))
+        P = np.zeros((len(agg), nc))
+        P[np.arange(len(agg)), agg] = w / norms[agg]
+        assert np.allclose(P.T @ P, np.eye(nc), atol=1e-14)
+        w = P.T @ w
+        Ak = P.T @ Ak @ P
+        mats.append(Ak)
+        Ps.append(P)
+        ws.append(w)
+    return mats, Ps, ws
+
+
+def test_w_normalised_prolongator_vcycle_equals_literal_construction():
+    A = W.diffusion7(5, 2.0, 11)  # aggregates of unequal sizes
+    hn = O.Hierarchy(A, coarse_size=8, aggr_steps=2, prolong_scale=O.PROLONG_W_NORMALIZED)
+    hu = O.Hierarchy(A, coarse_size=8, aggr_steps=2)
+    assert hn.num_levels == hu.num_levels >= 3
+    for k in range(hn.num_levels - 1):
+        assert np.array_equal(hn.level_agg(k), hu.level_agg(k))
+    mats, Ps, _ = _normalised_hierarchy(A, hn)
+
+    def err(k):  # I - B_k A_k on the normalised matrices, l1 of their own rows
+        Ak = mats[k]
+        S = np.eye(len(Ak)) - np.diag(1.0 / np.abs(Ak).sum(axis=1)) @ Ak
+        if k == len(mats) - 1:
+            return np.linalg.matrix_power(S, 20)
+        P = Ps[k]
+        Bc = (np.eye(len(mats[k + 1])) - err(k + 1)) @ np.linalg.inv(mats[k + 1])
+        S4 = np.linalg.matrix_power(S, 4)
+        return S4 @ (np.eye(len(Ak)) - P @ Bc @ P.T @ Ak) @ S4
+
+    Ad = A.to_scipy().toarray()
+    Bn = dense_B(hn, A.n)
+    assert np.allclose(np.eye(A.n) - Bn @ Ad, err(0), atol=1e-12)
+    assert np.allclose(Bn, Bn.T, atol=1e-13)
+    # with unequal aggregate sizes the two prolongator forms give different cycles
+    assert np.abs(Bn - dense_B(hu, A.n)).max() > 1e-6
+    # the learned part's gradient is defined for unit prolongators only
+    assert np.isnan(hn.loss_grad(W.random_vector(A.n, 1), 1)[0])
+
+
+def test_w_normalised_matching_weights_equal_unit_ones():
+    """The weight of Sec. 3.1 / reading 1 on (A_norm^k, w^k) equals the weight on
+    (A^k, 1) at every pairwise step (aggr_steps = 1: every step is a level), so
+    the normalisation leaves the matching unchanged."""
+    A = W.diffusion27(6, 2.0, 5)
+    h = O.Hierarchy(A, coarse_size=4, aggr_steps=1)
+    assert h.num_levels >= 4
+    mats, _, ws = _normalised_hierarchy(A, h)
+    for k in range(h.num_levels - 1):
+        rp, ci, v = h.level_csr(k)
+        unit = O.weights(rp, ci, v)
+        An, w = mats[k], ws[k]
+        rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+        off = rows != ci
+        a = An[rows, ci]
+        d = np.diag(An)
+        wn = 1.0 - 2.0 * a * w[rows] * w[ci] / (d[rows] * w[rows] ** 2 + d[ci] * w[ci] ** 2)
+        assert np.allclose(wn[off], unit[off], rtol=0, atol=1e-12)
+
+
+def test_w_normalised_equals_unit_on_equal_aggregate_sizes():
+    """All aggregates of a level of one size: w is constant per level, w_I / w_J = 1
+    exactly, and the two forms run the same arithmetic bit for bit."""
+    A = W.poisson7(8)
+    hn = O.Hierarchy(A, coarse_size=8, prolong_scale=O.PROLONG_W_NORMALIZED)
+    hu = O.Hierarchy(A, coarse_size=8)
+    assert hn.num_levels == 3
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 3))
+    rn, ru = hn.fcg(b), hu.fcg(b)
+    assert rn["iters"] == ru["iters"]
+    assert np.array_equal(rn["x"], ru["x"]) and np.array_equal(rn["hist"], ru["hist"])
+    with pytest.raises(ValueError):
+        O.Hierarchy(A, prolong_scale=2)
