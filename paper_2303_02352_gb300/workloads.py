@@ -204,6 +204,45 @@ def laplace1d(n: int) -> CSR:
     return CSR(n, row_ptr, c[mask].astype(np.int32), v[mask])
 
 
+def random_spd(n: int, seed: int, max_partners: int = 180, mixed_sign: bool = False,
+               isolated: float = 0.01) -> CSR:
+    """Unstructured sparse SPD matrix (a random graph, no grid).  Row i picks
+    p_i = 1 + floor((max_partners - 1) U^6) partners uniformly at random
+    (mostly a few, rarely up to max_partners) and the pattern is symmetrised,
+    so a row holds its own picks, the picks that name it and the diagonal:
+    with the default about 1 to 220 entries, median about 30; a fraction
+    ``isolated`` of the rows keeps the diagonal alone.  Off-diagonal
+    magnitudes k/64 (k = 1..64, so many equal weights), negative, or of random
+    sign with ``mixed_sign``; a_ii = sum_j |a_ij| + (1 + k')/64 (k' = 0..7),
+    strictly diagonally dominant and therefore SPD.  Every value is a multiple
+    of 1/64, so the diagonal sums are exact in any order."""
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    idx = np.arange(n, dtype=np.uint64)
+    deg = 1 + np.floor((max_partners - 1) * uniform01(seed, idx) ** 6).astype(np.int64)
+    deg[uniform01(seed + 1, idx) < isolated] = 0
+    src = np.repeat(np.arange(n, dtype=np.int64), deg)
+    dst = np.floor(uniform01(seed + 2, np.arange(len(src), dtype=np.uint64)) * n).astype(np.int64)
+    ok = (src != dst) & (deg[dst] > 0)
+    lo, hi = np.minimum(src[ok], dst[ok]), np.maximum(src[ok], dst[ok])
+    key = np.unique(lo * n + hi)
+    lo, hi = key // n, key % n
+    e = np.arange(len(key), dtype=np.uint64)
+    mag = (1.0 + np.floor(64.0 * uniform01(seed + 3, e))) / 64.0
+    sgn = np.where(uniform01(seed + 4, e) < 0.5, 1.0, -1.0) if mixed_sign else -np.ones(len(key))
+    off = sgn * mag
+    rows = np.concatenate([lo, hi, np.arange(n)])
+    cols = np.concatenate([hi, lo, np.arange(n)])
+    absum = np.bincount(lo, weights=mag, minlength=n) + np.bincount(hi, weights=mag, minlength=n)
+    diag = absum + (1.0 + np.floor(8.0 * uniform01(seed + 5, idx))) / 64.0
+    vals = np.concatenate([off, off, diag])
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    row_ptr = np.zeros(n + 1, dtype=np.int32)
+    row_ptr[1:] = np.cumsum(np.bincount(rows, minlength=n))
+    return CSR(n, row_ptr, cols.astype(np.int32), vals.astype(np.float64))
+
+
 def random_vector(n: int, seed: int) -> np.ndarray:
     """x_i = 2 U_i - 1 with U from stream ``seed``."""
     return 2.0 * uniform01(seed, np.arange(n, dtype=np.uint64)) - 1.0

@@ -28,6 +28,10 @@ CASES = [
     ("poisson32_tiled", "W.poisson7(32)", {}, {"AMG_PIPE": "0"}),
     ("diff7_20_wcycle", "W.diffusion7(20, 2.0, 1001)", {"cycle": 2}, {}),
     ("diff7_20_bf16", "W.diffusion7(20, 2.0, 1001)", {"precision": 2}, {}),
+    ("rand5k_mixed", "W.random_spd(5000, 8, mixed_sign=True)", {}, {}),
+    ("rand5k_mixed_bottom", "W.random_spd(5000, 8, mixed_sign=True)", {}, {"AMG_BOTTOM": "1"}),
+    ("rand20k_tiled", "W.random_spd(20000, 9)", {}, {"AMG_PIPE": "0"}),
+    ("rand20k_fp32", "W.random_spd(20000, 9)", {"precision": 1}, {}),
 ]
 
 RUNNER = r"""

@@ -675,3 +675,22 @@ def test_w_normalised_equals_unit_on_equal_aggregate_sizes():
     assert np.array_equal(rn["x"], ru["x"]) and np.array_equal(rn["hist"], ru["hist"])
     with pytest.raises(ValueError):
         O.Hierarchy(A, prolong_scale=2)
+
+
+def test_unstructured_workload_shape():
+    """The random-graph workload of the unstructured GPU cases has what they
+    rely on: rows of one entry (isolated) to a few hundred, a bitwise symmetric
+    pattern and values, strict diagonal dominance, and a coarse level whose
+    rows are longer than any pipelined tile of 8 rows holds."""
+    A = W.random_spd(5000, 7)
+    rl = np.diff(A.row_ptr)
+    assert rl.min() == 1 and rl.max() >= 150
+    S = A.to_scipy()
+    assert (S != S.T).nnz == 0
+    d = S.diagonal()
+    assert np.all(d > np.abs(S).sum(axis=1).A1 - d)
+    o = O.Hierarchy(A)
+    assert o.num_levels >= 2
+    assert np.diff(o.level_csr(1)[0]).max() > 256
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 3))
+    assert o.fcg(b)["status"] == O.OK
