@@ -132,7 +132,6 @@ struct amg_handle {
   int* zero_flag = nullptr;    // a device int that stays 0 (skip flag of standalone V-cycles)
   int red_grid = 0;            // persistent grid of the outer row kernels
   int ax_grid = 0;             // grid of the fused axpys
-  int stages = 2;              // pipeline depth of the row kernels (2 measured best: more stages cost resident blocks)
   int use_pipe = 1;            // 0: non-pipelined tiled row kernels
   int use_bottom = 2;          // bottom levels in one cluster launch: 0 never, 1 always (if they fit), 2 where the owner spread says it pays
   int small_rows = 0;          // levels with fewer rows use the non-pipelined tiled kernels

@@ -132,16 +132,17 @@ __device__ void load_level(const BotLevel& L, const BotLevel* C, const Ctx& c) {
   }
 }
 
-// s = sum_j a_ij x_j over row i (local index), x distributed at byte offset xo
+// r_i - sum_j a_ij x_j over row i (local index), accumulated from r_i like
+// the row kernels; x distributed at byte offset xo
 template <typename MT, typename VT>
-__device__ __forceinline__ VT row_dot(const BotLevel& L, const Ctx& c, int xo, int i) {
+__device__ __forceinline__ VT row_resid(const BotLevel& L, const Ctx& c, int xo, int i, VT ri) {
   const int32_t* rp = sec<int32_t>(c, L.o_rp);
   const int32_t* ci = sec<int32_t>(c, L.o_ci);
   const MT* v = sec<MT>(c, L.o_v);
-  VT s = 0;
+  VT s = ri;
   const int p1 = rp[i + 1];
 #pragma unroll 4
-  for (int p = rp[i]; p < p1; ++p) s += (VT)v[p] * dget<VT>(L, c, xo, ci[p]);
+  for (int p = rp[i]; p < p1; ++p) s -= (VT)v[p] * dget<VT>(L, c, xo, ci[p]);
   return s;
 }
 
@@ -161,7 +162,7 @@ __device__ int smooth(const BotLevel& L, const Ctx& c, int cur, int sweeps, bool
     } else {
       const VT* zi = sec<VT>(c, cur);
       for (int i = threadIdx.x; i < cnt; i += blockDim.x)
-        zo[i] = zi[i] + D[i] * (r[i] - row_dot<MT, VT>(L, c, cur, i));
+        zo[i] = zi[i] + D[i] * row_resid<MT, VT>(L, c, cur, i, r[i]);
     }
     cluster_barrier();
     cur = nxt;
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(BOT_THREADS) k_bottom(const __grid_constant__ 
     {
       const VT* r = sec<VT>(c, L.o_r);
       VT* t = sec<VT>(c, L.o_t);
-      for (int i = threadIdx.x; i < cnt; i += blockDim.x) t[i] = r[i] - row_dot<VT, VT>(L, c, zoff, i);
+      for (int i = threadIdx.x; i < cnt; i += blockDim.x) t[i] = row_resid<VT, VT>(L, c, zoff, i, r[i]);
     }
     cluster_barrier();
     if (k + 1 == nb - 1) restrict_to<VT, double>(L, C, c);

@@ -266,24 +266,24 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pair(const PairArg
       }
       const int av = p0 & ~(VE - 1), ac = p0 & ~3;
       const PipeTile<MT, 1>& T = P->st[stage];
-      VT s = 0;
+      VT s = rr;  // r_i - sum_j a_ij x_j accumulated from r_i, as in the single-pass kernel
       if (phase == 0) {
 #pragma unroll 8
-        for (int qq = q0; qq < q1; qq += TPR) s += (VT)to_acc(T.v[qq - av]) * __ldg(&a.z0[amg_chk(T.c[qq - ac], n)]);
+        for (int qq = q0; qq < q1; qq += TPR) s -= (VT)to_acc(T.v[qq - av]) * __ldg(&a.z0[amg_chk(T.c[qq - ac], n)]);
       } else {
 #pragma unroll 8
-        for (int qq = q0; qq < q1; qq += TPR) s += (VT)to_acc(T.v[qq - av]) * __ldcg(&a.z1[amg_chk(T.c[qq - ac], n)]);
+        for (int qq = q0; qq < q1; qq += TPR) s -= (VT)to_acc(T.v[qq - av]) * __ldcg(&a.z1[amg_chk(T.c[qq - ac], n)]);
       }
       if constexpr (TPR > 1) s = group_sum<TPR>(s);
       __syncwarp();
       if (lane == 0) mbar_arrive(&P->empty[stage]);
       if (phase == 0) {
-        if (lead) a.z1[row] = own + dd * (rr - s);
+        if (lead) a.z1[row] = own + dd * s;
         __syncwarp();
         if (lane == 0) red_release_add(&a.cnt[tile / PAIR_CHUNK], 1u);
       } else if (lead) {
-        if constexpr (MODE2 == PM_SWEEP) a.out[row] = (OT)(own + dd * (rr - s));
-        else a.out[row] = (OT)(rr - s);
+        if constexpr (MODE2 == PM_SWEEP) a.out[row] = (OT)(own + dd * s);
+        else a.out[row] = (OT)s;
       }
     }
   }

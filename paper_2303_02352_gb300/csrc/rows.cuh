@@ -306,20 +306,31 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
       }
       const int av = p0 & ~(VE - 1), ac = p0 & ~3;
       const PipeTile<MT, SB>& T = P->st[stage];
+      // sweeps and residuals accumulate r_i - sum_j a_ij x_j from r_i (the
+      // lead lane holds r_i, the others 0): one FP64 operation per row fewer
+      // than summing first and subtracting, on a part whose FP64 issue rate is
+      // a co-limit of these kernels
+      constexpr bool FROM_R = MODE == PM_SWEEP || MODE == PM_SWEEP_PROLONG || MODE == PM_RESID;
       VT s = 0;
+      if constexpr (FROM_R) {
+        s = rr;
 #pragma unroll 8
-      for (int q = q0; q < q1; q += TPR) s += (VT)to_acc(T.v[q - av]) * __ldg(&a.x[amg_chk(T.c[q - ac], n)]);
+        for (int q = q0; q < q1; q += TPR) s -= (VT)to_acc(T.v[q - av]) * __ldg(&a.x[amg_chk(T.c[q - ac], n)]);
+      } else {
+#pragma unroll 8
+        for (int q = q0; q < q1; q += TPR) s += (VT)to_acc(T.v[q - av]) * __ldg(&a.x[amg_chk(T.c[q - ac], n)]);
+      }
       if constexpr (TPR > 1) s = group_sum<TPR>(s);
       __syncwarp();
       if (lane == 0) mbar_arrive(&P->empty[stage]);  // this warp is done with the stage
       if (lead) {
         if constexpr (MODE == PM_SWEEP) {
-          a.out[row] = (OT)(own + dd * (rr - s));
+          a.out[row] = (OT)(own + dd * s);
         } else if constexpr (MODE == PM_SWEEP_PROLONG) {
-          zn = (OT)(own + dd * (rr - s));
+          zn = (OT)(own + dd * s);
           a.out[row] = zn;
         } else if constexpr (MODE == PM_RESID) {
-          a.out[row] = (OT)(rr - s);
+          a.out[row] = (OT)s;
         } else if constexpr (MODE == PM_SPMV) {
           a.out[row] = (OT)s;
         } else if constexpr (MODE == PM_DOTS) {

@@ -902,7 +902,7 @@ extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* str
   else amg_params_default(&h->p);
   h->stream = (cudaStream_t)stream;
   // test and tuning hooks (environment): AMG_PIPE=0 non-pipelined row kernels,
-  // AMG_STAGES pipeline depth, AMG_BOTTOM=0/1/2 bottom levels as separate
+  // AMG_BOTTOM=0/1/2 bottom levels as separate
   // launches / in one cluster launch / by the owner-spread rule (default),
   // AMG_FUSE=0 restriction and prolongation as separate kernels,
   // AMG_BIG=0 no 4x stages for FP64 long-row levels,
@@ -921,7 +921,6 @@ extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* str
   if (const char* e = getenv("AMG_PAIR_SLACK")) h->pair_slack = atoi(e);
   if (const char* e = getenv("AMG_FAIL_ALLOC_AFTER")) h->fail_alloc_after = atoi(e);
   if (const char* e = getenv("AMG_PIPE")) h->use_pipe = atoi(e);
-  if (const char* e = getenv("AMG_STAGES")) h->stages = atoi(e);
   amg_status st = setup_impl(h, A);
   if (st != AMG_OK) {
     amg_set_setup_error(h->err);
