@@ -306,11 +306,16 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
       }
       const int av = p0 & ~(VE - 1), ac = p0 & ~3;
       const PipeTile<MT, SB>& T = P->st[stage];
-      // sweeps and residuals accumulate r_i - sum_j a_ij x_j from r_i (the
-      // lead lane holds r_i, the others 0): one FP64 operation per row fewer
-      // than summing first and subtracting, on a part whose FP64 issue rate is
-      // a co-limit of these kernels
-      constexpr bool FROM_R = MODE == PM_SWEEP || MODE == PM_SWEEP_PROLONG || MODE == PM_RESID;
+      // residuals, and sweeps in standard stages, accumulate
+      // r_i - sum_j a_ij x_j from r_i (the lead lane holds r_i, the others 0):
+      // one FP64 operation per row fewer than summing first and subtracting, on
+      // a part whose FP64 issue rate is a co-limit of these kernels (7-point
+      // FP64 level-0 sweep 81.2 -> 80.2 us, level 1 11.8 -> 11.0 us, 27-point
+      // residual 185.6 -> 176.9 us).  Sweeps in the long-row forms (SB > 1: one
+      // block per multiprocessor, 8 consumer warps) sum first: starting from
+      // r_i made the 27-point FP64 sweep 166 -> 199 us there (measured).
+      constexpr bool FROM_R =
+          MODE == PM_RESID || ((MODE == PM_SWEEP || MODE == PM_SWEEP_PROLONG) && SB == 1 && NG == 1);
       VT s = 0;
       if constexpr (FROM_R) {
         s = rr;
@@ -325,12 +330,12 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
       if (lane == 0) mbar_arrive(&P->empty[stage]);  // this warp is done with the stage
       if (lead) {
         if constexpr (MODE == PM_SWEEP) {
-          a.out[row] = (OT)(own + dd * s);
+          a.out[row] = (OT)(own + dd * (FROM_R ? s : rr - s));
         } else if constexpr (MODE == PM_SWEEP_PROLONG) {
-          zn = (OT)(own + dd * s);
+          zn = (OT)(own + dd * (FROM_R ? s : rr - s));
           a.out[row] = zn;
         } else if constexpr (MODE == PM_RESID) {
-          a.out[row] = (OT)s;
+          a.out[row] = (OT)(FROM_R ? s : rr - s);
         } else if constexpr (MODE == PM_SPMV) {
           a.out[row] = (OT)s;
         } else if constexpr (MODE == PM_DOTS) {

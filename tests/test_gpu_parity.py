@@ -387,19 +387,24 @@ def test_long_row_kernel_forms(form, name, monkeypatch):
     assert G(A, precision=1).pcg_solve(b)["true_rel_res"] < 1e-6
 
 
-def test_automatic_kernel_forms(big):
-    """The setup's automatic choices: one thread per row in 4x stages for the
-    27-point FP64 fine level (64^3), standard stages for 7-point, and the fused
-    bottom for the regular 7-point 160^3 hierarchy (levels of 8,000 and 4,000
-    rows) but not for the irregular 27-point one (owner-spread rule).  Small
-    grids whose bottom levels are mostly boundary rows may decline it too."""
+def test_automatic_kernel_forms(big, monkeypatch):
+    """The setup's automatic choices: standard stages everywhere by default
+    (the 27-point FP64 fine level of 64^3 in 64-row tiles, 4 threads per row;
+    7-point in 256-row tiles), the fused bottom for the regular 7-point 160^3
+    hierarchy (levels of 8,000 and 4,000 rows) but not for the irregular
+    27-point one (owner-spread rule).  With the 4x-stage form switched on
+    (AMG_BIG=4) it takes the 27-point FP64 fine level, only on levels with at
+    least one 256-row tile per multiprocessor and never in FP32."""
     p = big[1].info()
     assert p["tile_rows"][0] == 256 and p["stage_scale"][0] == 1
     assert p["bottom_level"] == 3 and p["num_levels"] == 5
     d27 = W.diffusion27(64, 2.0, 3)
     d = G(d27).info()
-    assert d["tile_rows"][0] == 256 and d["stage_scale"][0] == 4
+    assert d["tile_rows"][0] == 64 and all(sc == 1 for sc in d["stage_scale"])
     assert d["bottom_level"] == d["num_levels"]
+    monkeypatch.setenv("AMG_BIG", "4")
+    d = G(d27).info()
+    assert d["tile_rows"][0] == 256 and d["stage_scale"][0] == 4
     # levels with fewer 256-row tiles than multiprocessors keep standard stages
     assert all(sc == 1 for n, sc in zip(d["n"], d["stage_scale"]) if n < 256 * 152)
     # low precision: the float fine level keeps standard stages

@@ -90,7 +90,7 @@ FORMS = [
     {"AMG_BOTTOM": "1"},                      # fused bottom whatever the owner spread
     {"AMG_BOTTOM": "0"},                      # bottom levels as separate launches
     {"AMG_FUSE": "0"},                        # restriction / prolongation as separate kernels
-    {"AMG_BIG": "0"}, {"AMG_BIG": "2"}, {"AMG_BIG": "5"},
+    {"AMG_BIG": "4"}, {"AMG_BIG": "2"}, {"AMG_BIG": "5"},    # the long-row forms (off by default)
     {"AMG_MIN_TPR": "4"}, {"AMG_MIN_TPR": "32"},
     {"AMG_SMALL_ROWS": "100000000"},          # pipelined forms off on every level
 ]
