@@ -130,10 +130,16 @@ class Hierarchy:
     def __init__(self, A, stream=None, **params):
         import torch
         self._torch = torch
+        sparse = isinstance(A, torch.Tensor) and A.layout == torch.sparse_csr
+        if sparse:
+            if A.dim() != 2 or A.shape[0] != A.shape[1]:
+                raise ValueError(f"A must be a square matrix, got shape {tuple(A.shape)}")
+            if A.values().numel() >= 2 ** 31:
+                raise ValueError("A has 2^31 or more stored entries (int32 indices)")
         lib = load()
         self._lib = lib
         dev = torch.device("cuda", torch.cuda.current_device())
-        if isinstance(A, torch.Tensor) and A.layout == torch.sparse_csr:
+        if sparse:
             rp = A.crow_indices().to(device=dev, dtype=torch.int32).contiguous()
             ci = A.col_indices().to(device=dev, dtype=torch.int32).contiguous()
             v = A.values().to(device=dev, dtype=torch.float64).contiguous()

@@ -64,3 +64,12 @@ def test_structs_match_header_layout(lib):
     body = re.findall(r"typedef struct \{([^{}]*?)\} amg_params;", src, re.S)[0]
     fields = re.findall(r"int32_t\s+(\w+);", body)
     assert tuple(fields) == amg.PARAM_FIELDS
+
+
+def test_binding_rejects_non_square_sparse_tensor_before_any_gpu_call():
+    import torch
+    from paper_2303_02352_gb300 import amg
+    A = torch.sparse_csr_tensor(torch.tensor([0, 1, 2]), torch.tensor([0, 1]),
+                                torch.tensor([1.0, 1.0], dtype=torch.float64), size=(2, 3))
+    with pytest.raises(ValueError, match="square"):
+        amg.setup(A)
