@@ -1,5 +1,7 @@
-"""Replica plumbing of bench.py on CPU: two gloo ranks, barrier and the maximum
-over ranks of the per-rank step time (what the benchmark reports for N > 1)."""
+"""bench.py on CPU: the replica plumbing (two gloo ranks, barrier and the
+maximum over ranks of the per-rank step time, what the benchmark reports for
+N > 1) and the reference arm (the oracle on the host cores: its JSON line, and
+ranks other than 0 leaving without output)."""
 import os
 import socket
 
@@ -53,3 +55,37 @@ def test_single_process_defaults(monkeypatch):
     assert d.max(3.5) == 3.5
     d.barrier()
     d.close()
+
+
+def _bench(args, env_extra=None):
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ)
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        env.pop(k, None)
+    env.update(env_extra or {})
+    return subprocess.run([sys.executable, os.path.join(root, "bench.py"), *args], env=env, cwd=root,
+                          capture_output=True, text=True, timeout=600)
+
+
+def test_reference_arm_line_on_cpu():
+    """`bench.py --impl reference` (the oracle timed on the host cores) prints
+    one JSON line with the contract's keys; it needs no GPU."""
+    import json
+    r = _bench(["--impl", "reference", "--workload", "poisson32", "--steps", "2", "--warmup", "1"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "ms" and d["value"] > 0
+    assert d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is False
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["iters"] > 0 and "32^3" in d["config"]["workload"]
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    r = _bench(["--impl", "reference", "--workload", "poisson32", "--steps", "1", "--warmup", "0"],
+               {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert r.returncode == 0 and not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
