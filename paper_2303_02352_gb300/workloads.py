@@ -205,7 +205,7 @@ def laplace1d(n: int) -> CSR:
 
 
 def random_spd(n: int, seed: int, max_partners: int = 180, mixed_sign: bool = False,
-               isolated: float = 0.01) -> CSR:
+               isolated: float = 0.01, zero_frac: float = 0.0) -> CSR:
     """Unstructured sparse SPD matrix (a random graph, no grid).  Row i picks
     p_i = 1 + floor((max_partners - 1) U^6) partners uniformly at random
     (mostly a few, rarely up to max_partners) and the pattern is symmetrised,
@@ -215,7 +215,9 @@ def random_spd(n: int, seed: int, max_partners: int = 180, mixed_sign: bool = Fa
     magnitudes k/64 (k = 1..64, so many equal weights), negative, or of random
     sign with ``mixed_sign``; a_ii = sum_j |a_ij| + (1 + k')/64 (k' = 0..7),
     strictly diagonally dominant and therefore SPD.  Every value is a multiple
-    of 1/64, so the diagonal sums are exact in any order."""
+    of 1/64, so the diagonal sums are exact in any order.  With ``zero_frac``,
+    that fraction of the off-diagonal pairs keeps its place in the pattern
+    with the value 0.0 (explicit zeros)."""
     if n < 1:
         raise ValueError("n must be >= 1")
     idx = np.arange(n, dtype=np.uint64)
@@ -229,6 +231,8 @@ def random_spd(n: int, seed: int, max_partners: int = 180, mixed_sign: bool = Fa
     lo, hi = key // n, key % n
     e = np.arange(len(key), dtype=np.uint64)
     mag = (1.0 + np.floor(64.0 * uniform01(seed + 3, e))) / 64.0
+    if zero_frac > 0.0:
+        mag[uniform01(seed + 6, e) < zero_frac] = 0.0
     sgn = np.where(uniform01(seed + 4, e) < 0.5, 1.0, -1.0) if mixed_sign else -np.ones(len(key))
     off = sgn * mag
     rows = np.concatenate([lo, hi, np.arange(n)])

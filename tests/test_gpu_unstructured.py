@@ -1,7 +1,9 @@
 """Unstructured matrices against the oracle, through the C ABI: random graphs
 (no grid) with rows of 1 to about 220 entries, isolated rows (the diagonal
 alone), many equal matching weights (values on a 1/64 grid), mixed-sign
-off-diagonals, and coarse levels whose rows hold hundreds of entries (rows too
+off-diagonals, explicit zeros in the pattern (never matched; coarse entries
+that cancel to zero are kept), and coarse levels whose rows hold hundreds of
+entries (rows too
 long for the pipelined tiles, so the fallback row kernels and the fused bottom
 see them).  Same bars as the structured problems: hierarchy bit-exact, one
 V-cycle to 1e-12, SpMV to 1e-13, FCG iterations within 1 and the iterate at the
@@ -21,6 +23,7 @@ RAND = {
     "rand5k_mixed": lambda: W.random_spd(5000, 8, mixed_sign=True),
     "rand20k": lambda: W.random_spd(20000, 9),
     "rand3k_light": lambda: W.random_spd(3001, 10, max_partners=12),
+    "rand4k_zeros": lambda: W.random_spd(4000, 21, mixed_sign=True, zero_frac=0.3),  # explicit zeros
     "rand7": lambda: W.random_spd(7, 12, mixed_sign=True),
     "rand1": lambda: W.random_spd(1, 11),
 }

@@ -694,3 +694,27 @@ def test_unstructured_workload_shape():
     assert np.diff(o.level_csr(1)[0]).max() > 256
     b = W.rhs_from_solution(A, W.random_vector(A.n, 3))
     assert o.fcg(b)["status"] == O.OK
+
+
+def test_explicit_zeros_are_not_edges():
+    """Reading 1: a stored entry with the value 0.0 is no edge of the matching
+    graph (weight 0, never matched), and the Galerkin product keeps the
+    structural zeros and the cancellations it produces."""
+    A = W.random_spd(600, 21, mixed_sign=True, zero_frac=0.3)
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    zero = (A.val == 0.0) & (rows != A.col_idx)
+    assert zero.sum() > 100
+    wgt = O.weights(A.row_ptr, A.col_idx, A.val)
+    assert np.all(wgt[zero] == 0.0) and np.all(wgt[~zero & (rows != A.col_idx)] > 0.0)
+    mate = O.match_greedy(A.row_ptr, A.col_idx, wgt)
+    S = A.to_scipy()
+    for i in np.flatnonzero(mate >= 0):
+        assert S[i, mate[i]] != 0.0
+    # pattern of A_c = P^T |pattern| P, values = P^T A P with the zeros kept
+    agg, nc = O.aggregate(mate)
+    rpc, cic, vc = O.galerkin(A.row_ptr, A.col_idx, A.val, agg, nc)
+    P = sp.csr_matrix((np.ones(A.n), (np.arange(A.n), agg)), shape=(A.n, nc))
+    pat = (P.T @ sp.csr_matrix((np.ones(A.nnz), A.col_idx, A.row_ptr), shape=(A.n, A.n)) @ P).tocsr()
+    pat.sort_indices()
+    assert np.array_equal(rpc, pat.indptr) and np.array_equal(cic, pat.indices)
+    assert np.allclose(dense(rpc, cic, vc, nc), (P.T @ S @ P).toarray(), rtol=0, atol=1e-13)
