@@ -152,17 +152,12 @@ def _autograd():
 MLPFn, VCycleFn, SpMVFn = _autograd()
 
 
-def _ensure():
-    """Kept for callers of the earlier lazy form: the Functions exist at import."""
-
-
 def level_features(h):
     return [h.features(k) for k in range(h.num_levels)]
 
 
 def stationary_loss(h, omegas, r0, m: int):
     """(1/m) ln(|r_m| / |r_0|) with r_{t+1} = r_t - A B(omega) r_t."""
-    _ensure()
     import torch
     r = r0
     for _ in range(m):
@@ -175,7 +170,6 @@ def train(problems, steps: int = 200, m: int = 3, lr: float = 3e-3, seed: int = 
           log=None):
     """Trains the network on hierarchies built by the library.  problems: list
     of CSR matrices.  Returns (net, losses)."""
-    _ensure()
     import torch
     from . import workloads as W
     net = net or Network(init_theta(seed))

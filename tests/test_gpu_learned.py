@@ -60,7 +60,6 @@ def test_network_forward_backward_and_adam_match_reference():
     n = 1000
     feats = torch.tensor(rng.standard_normal((n, 4)), dtype=torch.float32, device="cuda")
     th = net.theta.detach().requires_grad_(True)
-    L._ensure()
     om = L.MLPFn.apply(feats, th, net.w)
     ref = M.forward(wq, feats.cpu().numpy().astype(np.float64))
     assert rel(om.detach().cpu().numpy(), ref) < 1e-5
