@@ -718,3 +718,44 @@ def test_explicit_zeros_are_not_edges():
     pat.sort_indices()
     assert np.array_equal(rpc, pat.indptr) and np.array_equal(cic, pat.indices)
     assert np.allclose(dense(rpc, cic, vc, nc), (P.T @ S @ P).toarray(), rtol=0, atol=1e-13)
+
+
+def _laplace1d_l1_four(n):
+    """tridiag(-1, 2, -1) with 3 in the two corner diagonal entries: every l1
+    row norm is 4 on every level of its hierarchy (pairwise Galerkin keeps
+    the form), so D = 1/4 and small-integer inputs keep every intermediate
+    of a short V-cycle exact in float32."""
+    A = W.laplace1d(n)
+    v = A.val.copy()
+    for i in (0, n - 1):
+        for p in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            if A.col_idx[p] == i:
+                v[p] = 3.0
+    return W.CSR(n, A.row_ptr, A.col_idx, v)
+
+
+@pytest.mark.parametrize("kw,levels", [
+    (dict(coarse_size=4, aggr_steps=1, pre_sweeps=1, post_sweeps=2, coarse_sweeps=2), 4),
+    (dict(coarse_size=4, aggr_steps=2, pre_sweeps=2, post_sweeps=2, coarse_sweeps=2), 3),
+    (dict(coarse_size=4, aggr_steps=2, pre_sweeps=1, post_sweeps=1, coarse_sweeps=1, cycle=2), 3),
+])
+def test_low_precision_vcycle_equals_fp64_in_exact_arithmetic(kw, levels):
+    """The float V-cycle of the mixed-precision emulation is separate code from
+    the FP64 one; where no operation rounds (values, D = 1/4 and the
+    intermediates of small-integer inputs are all exact in float32 and bf16),
+    both must give the same bits, so a dropped term, a wrong index or a
+    missing sweep in the float path shows up; with a generic input they differ
+    by float32 rounding only."""
+    A = _laplace1d_l1_four(16)
+    hd = O.Hierarchy(A, **kw)
+    assert hd.num_levels == levels
+    assert all(np.all(hd.level_l1(k) == 4.0) for k in range(levels))
+    r = np.floor(W.random_vector(A.n, 5) * 4)
+    zd = hd.vcycle(r)
+    rg = W.random_vector(A.n, 6)
+    zg = hd.vcycle(rg)
+    for prec in (O.FP32, O.FP32_BF16FINE):
+        hf = O.Hierarchy(A, precision=prec, **kw)
+        assert np.array_equal(hf.vcycle(r), zd)
+        zf = hf.vcycle(rg)
+        assert not np.array_equal(zf, zg) and np.linalg.norm(zf - zg) < 1e-6 * np.linalg.norm(zg)
