@@ -104,16 +104,14 @@ class Clocks:
             fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL,
+                                          "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL,
                                          stderr=subprocess.DEVNULL)
-            time.sleep(0.3)
         except Exception:
             self.proc = None
 
     def stop(self) -> dict | None:
         if not self.proc:
             return None
-        time.sleep(0.25)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -141,7 +139,8 @@ class Clocks:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(num(r[2]) for r in rows),
-                "power_w_max": max(num(r[3]) for r in rows), "samples": len(rows), "reasons": reasons}
+                "power_w_max": max(num(r[3]) for r in rows), "samples": len(rows), "reasons": reasons,
+                "window": "every 100 ms over the timed steps and 0.5 s of the same solves before and after"}
 
 
 def gpu_index(local_rank: int) -> int:
@@ -290,10 +289,18 @@ def main():
         raise SystemExit(f"solve did not converge: {res}")
     iters = res["iters"]
 
+    def load(seconds):
+        # the same solves, untimed, so that the clock samples around the short
+        # timed region are taken with the GPU under the same load
+        t_end = time.perf_counter() + seconds
+        while time.perf_counter() < t_end:
+            solve()
+
     clocks = Clocks(gpu_index(local))
+    clocks.start()
+    load(0.5)
     dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
@@ -303,6 +310,7 @@ def main():
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     dist.barrier()
+    load(0.5)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     ms = dist.max(ms)
