@@ -117,30 +117,36 @@ class Clocks:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
         try:
-            for line in open(self.path):
-                f = [x.strip() for x in line.split(",")]
-                if len(f) >= 9 and f[0] == str(self.idx):
-                    rows.append(f)
+            lines = open(self.path).read().splitlines()
             os.unlink(self.path)
         except Exception:
             return None
-        if not rows:
-            return None
+        return parse_clocks(lines, self.idx)
 
-        def num(x):
-            try:
-                return float(x)
-            except ValueError:
-                return float("nan")
 
-        sm = [num(r[1]) for r in rows]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower().startswith("active")})
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(num(r[2]) for r in rows),
-                "power_w_max": max(num(r[3]) for r in rows), "samples": len(rows), "reasons": reasons,
-                "window": "every 100 ms over the timed steps and 0.5 s of the same solves before and after"}
+def parse_clocks(lines, idx: int) -> dict | None:
+    """Summary of nvidia-smi samples (Clocks.FIELDS, csv, no header) of GPU idx."""
+    rows = []
+    for line in lines:
+        f = [x.strip() for x in line.split(",")]
+        if len(f) >= 9 and f[0] == str(idx):
+            rows.append(f)
+    if not rows:
+        return None
+
+    def num(x):
+        try:
+            return float(x)
+        except ValueError:
+            return float("nan")
+
+    sm = [num(r[1]) for r in rows]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower().startswith("active")})
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(num(r[2]) for r in rows),
+            "power_w_max": max(num(r[3]) for r in rows), "samples": len(rows), "reasons": reasons,
+            "window": "every 100 ms over the timed steps and 0.5 s of the same solves before and after"}
 
 
 def gpu_index(local_rank: int) -> int:

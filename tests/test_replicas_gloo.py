@@ -1,4 +1,4 @@
-"""bench.py on CPU: the replica plumbing (two gloo ranks, barrier and the
+"""bench.py on CPU: the clock-sample summary, the replica plumbing (two gloo ranks, barrier and the
 maximum over ranks of the per-rank step time, what the benchmark reports for
 N > 1) and the reference arm (the oracle on the host cores: its JSON line, and
 ranks other than 0 leaving without output)."""
@@ -89,3 +89,22 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = _bench(["--impl", "reference", "--workload", "poisson32", "--steps", "1", "--warmup", "0"],
                {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0 and not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_clock_samples_summary():
+    """The clock record of the bench line: median SM clock under load, the
+    highest max clock and power, and every throttle reason seen active, for
+    the bench's own GPU only."""
+    import bench
+    lines = [
+        "0, 2070, 2070, 700.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "1, 1200, 2070, 300.0, 0x0000000000000008, Active, Not Active, Not Active, Not Active",
+        "0, 2010, 2070, 810.9, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 650.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ]
+    c = bench.parse_clocks(lines, 0)
+    assert c["samples"] == 3 and c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
+    assert c["power_w_max"] == 810.9 and c["reasons"] == ["sw_power_cap"]
+    assert bench.parse_clocks(lines, 1)["reasons"] == ["hw_slowdown"]
+    assert bench.parse_clocks(lines, 5) is None
