@@ -1,7 +1,7 @@
-"""bench.py on CPU: the clock-sample summary, the replica plumbing (two gloo ranks, barrier and the
-maximum over ranks of the per-rank step time, what the benchmark reports for
-N > 1) and the reference arm (the oracle on the host cores: its JSON line, and
-ranks other than 0 leaving without output)."""
+"""bench.py on CPU: the clock-sample summary, the replica plumbing (two gloo
+ranks, barrier and the maximum over ranks of the per-rank step time, what the
+benchmark reports for N > 1) and the reference arm (the oracle on the host
+cores: its JSON line, and ranks other than 0 leaving without output)."""
 import os
 import socket
 
