@@ -1,5 +1,5 @@
 """Learned l1-Jacobi damping: the network, its training through the V-cycle
-adjoint, and the judge that keeps it only where it beats plain l1-Jacobi.
+adjoint, and the selection that keeps it only where it beats plain l1-Jacobi.
 
 The damping omega_i in (0, 2) of row i on level k multiplies the l1-Jacobi
 diagonal, D_i = omega_i / M_ii (M_ii = sum_j |a_ij|, Sec. 3.1).  A network
@@ -193,7 +193,7 @@ def train(problems, steps: int = 200, m: int = 3, lr: float = 3e-3, seed: int = 
     return net, losses
 
 
-def judge(A, b, net: Network, tol=1e-6, maxit=1000, **params):
+def choose_damping(A, b, net: Network, tol=1e-6, maxit=1000, **params):
     """Solves with plain l1-Jacobi and with the learned damping; keeps the
     learned one only if it needs no more iterations.  Returns a dict."""
     import torch

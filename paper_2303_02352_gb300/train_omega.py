@@ -6,7 +6,7 @@ Recipe: 64 seeded 7-point random-coefficient problems on 64^3 grids
 1000 + p), objective (1/m) ln(|r_m| / |r_0|) of m = 3 stationary V-cycle steps
 from seeded random r_0, Adam; then PCG to 1e-6 on a held-out 7-point
 log-normal problem (sigma = 2, seed 4000) and on 7-point Poisson, with the FP32
-and FP64 hierarchies, plain vs learned (the judge keeps the learned damping
+and FP64 hierarchies, plain vs learned (the selection keeps the learned damping
 only if it needs no more iterations).
 
     python -m paper_2303_02352_gb300.train_omega [--problems 64] [--N 64] [--epochs 5]
@@ -49,7 +49,7 @@ def evaluate(net, A, b_np, desc, precisions=(1, 0)):
         name = {0: "fp64", 1: "fp32", 2: "bf16fine"}[prec]
         out[name] = {"plain_iters": rp["iters"], "plain_ms": ms_p, "plain_true_rel_res": rp["true_rel_res"],
                      "learned_iters": rl["iters"], "learned_ms": ms_l, "learned_true_rel_res": rl["true_rel_res"],
-                     "judge_keeps_learned": use}
+                     "learned_kept": use}
         h.close()
     return out
 

@@ -146,37 +146,37 @@ def test_adjoint_against_finite_differences_on_gpu():
             assert abs(fd - float(omt[k].grad[i])) <= 1e-5 * max(abs(fd), 1e-3), (k, i)
 
 
-def test_training_gains_over_plain_and_judge_falls_back():
+def test_training_gains_over_plain_and_selection_falls_back():
     from paper_2303_02352_gb300 import learned as L
     probs = [W.training_problem(p, N=20) for p in range(6)]
     net, losses = L.train(probs, steps=60, m=3, lr=1e-2, seed=0)
     assert np.mean(losses[-6:]) < np.mean(losses[:6]) - 0.02
     A = W.diffusion7(28, 2.0, 4242)
     b = W.rhs_from_solution(A, W.random_vector(A.n, 1))
-    res = L.judge(A, b, net)
+    res = L.choose_damping(A, b, net)
     assert res["learned"]["status"] == 0 and res["learned"]["true_rel_res"] < 1e-6
     assert res["learned_iters"] < res["plain_iters"], (res["learned_iters"], res["plain_iters"])
     assert res["use_learned"]
-    # a network that damps everything to almost zero is worse: the judge keeps plain
+    # a network that damps everything to almost zero is worse: the selection keeps plain
     bad = L.init_theta(0)
     bad[-1] = -8.0
-    res2 = L.judge(A, b, L.Network(bad), maxit=60)
+    res2 = L.choose_damping(A, b, L.Network(bad), maxit=60)
     assert not res2["use_learned"]
     z_plain = L._amg.Hierarchy(A).vcycle(W.random_vector(A.n, 3)).cpu().numpy()
-    z_judged = res2["handle"].vcycle(W.random_vector(A.n, 3)).cpu().numpy()
-    assert np.array_equal(z_plain.view(np.uint64), z_judged.view(np.uint64))
+    z_chosen = res2["handle"].vcycle(W.random_vector(A.n, 3)).cpu().numpy()
+    assert np.array_equal(z_plain.view(np.uint64), z_chosen.view(np.uint64))
 
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_committed_network_gains_at_full_size(prec):
     """The shipped weights on the learned-smoother evaluation problem (7-point
     log-normal diffusion 256^3, sigma 2, 16.8M rows): fewer iterations than
-    plain l1-Jacobi to the true FP64 1e-6, kept by the judge, in the FP64 and
+    plain l1-Jacobi to the true FP64 1e-6, kept by the selection, in the FP64 and
     FP32 hierarchies."""
     from paper_2303_02352_gb300 import learned as L
     net = L.Network.load()
     A, b, _ = W.config("diffusion7_256")
-    res = L.judge(A, b, net, precision=prec)
+    res = L.choose_damping(A, b, net, precision=prec)
     assert res["learned"]["status"] == 0 and res["learned"]["true_rel_res"] < 1e-6
     assert res["learned_iters"] < res["plain_iters"], (res["learned_iters"], res["plain_iters"])
     assert res["use_learned"]
