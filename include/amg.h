@@ -97,7 +97,7 @@ typedef struct {
 
 typedef struct amg_handle amg_handle;
 
-/* Fills *p with the defaults above. */
+/* Fills *p with the defaults above (the settings of Sec. 5 and Listing 1). */
 void amg_params_default(amg_params* p);
 
 /*
@@ -123,8 +123,8 @@ amg_status amg_setup(const amg_csr* A, const amg_params* p, void* stream, amg_ha
 amg_status amg_pcg_solve(amg_handle* h, const double* b, double* x, double tol, int32_t maxit,
                          int32_t* iters, double* res_hist, double* true_rel_res);
 
-/* Same as amg_pcg_solve with b and x in host memory: the host-to-device copy of
- * b and x and the device-to-host copy of x are part of the call. */
+/* Alg. 1 as amg_pcg_solve, with b and x in host memory: the host-to-device copy
+ * of b and x and the device-to-host copy of x are part of the call. */
 amg_status amg_pcg_solve_host(amg_handle* h, const double* b_host, double* x_host, double tol,
                               int32_t maxit, int32_t* iters, double* res_hist, double* true_rel_res);
 
@@ -136,18 +136,24 @@ amg_status amg_cg_solve(amg_handle* h, const double* b, double* x, double tol, i
  * distinct buffers. */
 amg_status amg_vcycle(amg_handle* h, const double* r, double* z);
 
-/* y = A^k x for hierarchy level k.  x, y: device, n_k, distinct buffers. */
+/* y = A^k x for hierarchy level k (A^0 = A; A^{k+1} the Galerkin operator of
+ * Alg. 3 / Sec. 3.1).  x, y: device, n_k, distinct buffers. */
 amg_status amg_spmv(amg_handle* h, int32_t level, const double* x, double* y);
 
-/* Hierarchy summary (host struct). */
+/* Hierarchy summary (host struct): levels, sizes and the operator complexity
+ * the paper reports (Sec. 5), setup timings, kernel forms. */
 amg_status amg_info(const amg_handle* h, amg_info_t* info);
 
 /* Copies of the hierarchy to host memory.  agg_host: n_k ints, the level-k row
- * -> level-(k+1) row map (level < num_levels-1).  CSR: n_k+1, nnz_k, nnz_k. */
+ * -> level-(k+1) row map (level < num_levels-1): the aggregates of Alg. 3
+ * composed over the s pairwise steps of a level (Sec. 3.1), i.e. the column
+ * of the prolongator's single unit entry in each row.  CSR: n_k+1, nnz_k,
+ * nnz_k (the level matrix A^k). */
 amg_status amg_get_aggregates(amg_handle* h, int32_t level, int32_t* agg_host);
 amg_status amg_get_level_csr(amg_handle* h, int32_t level, int32_t* row_ptr_host,
                              int32_t* col_idx_host, double* val_host);
-/* l1 row norms M_ii = sum_j |a_ij| of level k (host, n_k doubles). */
+/* l1 row norms M_ii = sum_j |a_ij| of level k, the l1-Jacobi diagonal of
+ * Sec. 3.1 (host, n_k doubles). */
 amg_status amg_get_l1(amg_handle* h, int32_t level, double* l1_host);
 
 /*
