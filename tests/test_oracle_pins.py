@@ -423,6 +423,71 @@ def test_fcg_zero_rhs_and_maxit():
 
 
 # ----------------------------------------------------------------------------
+# periodic true-residual replacement of the low-precision hierarchy (r <- b - A u
+# every k iterations; the recurrences of Alg. 1 are otherwise unchanged)
+
+def _true_residuals(h, A, b, iters):
+    """|b - A u_it| / |b| by scipy for the iterates u_it of h.fcg(tol=0, maxit=it)."""
+    S, nb = A.to_scipy(), np.linalg.norm(b)
+    return {it: np.linalg.norm(b - S @ h.fcg(b, tol=0.0, maxit=it)["x"]) / nb for it in iters}
+
+
+@pytest.mark.parametrize("prec,k", [(O.FP32, 2), (O.FP32, 3), (O.FP32_BF16FINE, 3), (O.FP32_BF16FINE, 4)])
+def test_periodic_true_residual_replacement_iterations_and_values(prec, k):
+    """Run far past convergence (tol = 0): the recursive residual of Alg. 1 keeps
+    falling geometrically while b - A u stagnates at round-off.  A replacement
+    therefore shows as a rise of the history back to the true residual, exactly
+    at the multiples of k; between replacements the history falls again."""
+    A = W.poisson7(14)
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 3))
+    M = 45
+    h = O.Hierarchy(A, precision=prec, true_res_every=k)
+    hist = h.fcg(b, tol=0.0, maxit=M)["hist"]
+    plain = O.Hierarchy(A, precision=prec, true_res_every=0).fcg(b, tol=0.0, maxit=M)["hist"]
+    # the same recurrences up to the first replacement
+    assert np.array_equal(hist[:k], plain[:k])
+    stag = int(np.argmax(plain < 1e-20))  # the recursive residual has left the true one far behind
+    assert 10 <= stag < M - 2 * k
+    tr = _true_residuals(h, A, b, range(1, M + 1))
+    noise = np.median([tr[it] for it in range(stag, M + 1)])
+    assert noise < 1e-14
+    for it in range(stag, M + 1):
+        if it % k == 0:
+            # replaced: the history holds |b - A u_it| (two summation orders of a
+            # round-off-level quantity agree to a small factor), above its predecessor
+            assert 0.25 < hist[it] / tr[it] < 4.0, (it, hist[it], tr[it])
+            assert hist[it] > hist[it - 1], it
+        else:
+            # recursive steps after the last replacement: below it
+            assert hist[it] < hist[it - (it % k)], it
+    # without replacement the recursive residual ends far below the true one
+    assert plain[M] < 1e-3 * noise
+    # before stagnation each replaced entry is the true residual of u_it itself
+    # (a residual of u_{it-1} would be a convergence factor off)
+    for it in range(k, stag - 4, k):
+        assert abs(hist[it] - tr[it]) <= 1e-8 * tr[it], (it, hist[it], tr[it])
+        assert abs(hist[it] - hist[it - 1]) > 0.5 * hist[it]
+
+
+def test_true_residual_replacement_only_in_low_precision_and_solves_converge():
+    A = W.diffusion7(12, 2.0, 5)
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 3))
+    ref64 = O.Hierarchy(A).fcg(b, tol=0.0, maxit=30)["hist"]
+    for k in (1, 2, 3):
+        # FP64 hierarchy: the recursive residual is never replaced
+        r64 = O.Hierarchy(A, true_res_every=k).fcg(b, tol=0.0, maxit=30)
+        assert np.array_equal(r64["hist"], ref64)
+    for prec in (O.FP32, O.FP32_BF16FINE):
+        base = O.Hierarchy(A, precision=prec, true_res_every=0).fcg(b)
+        for k in (1, 2, 3):
+            res = O.Hierarchy(A, precision=prec, true_res_every=k).fcg(b)
+            assert res["status"] == O.OK and res["true_rel_res"] < 1e-6
+            assert abs(res["iters"] - base["iters"]) <= 1
+            nb = np.linalg.norm(b)
+            assert abs(res["true_rel_res"] - np.linalg.norm(b - A.to_scipy() @ res["x"]) / nb) < 1e-12
+
+
+# ----------------------------------------------------------------------------
 # mixed precision emulation and bf16 rounding
 
 
@@ -480,6 +545,24 @@ def test_loss_gradient_matches_finite_differences():
             h.set_omega(k, om[k])
             fd = (Lp - Lm) / (2 * eps)
             assert abs(fd - g[k][i]) <= 1e-5 * max(abs(fd), 1e-3), (k, i, fd, g[k][i])
+
+
+@pytest.mark.parametrize("m", [1, 3])
+def test_loss_equals_dense_stationary_iteration(m):
+    """The training loss is (1/m) ln(|(I - A B)^m r0| / |r0|): m steps of the
+    stationary iteration r <- r - A B r, with B the V-cycle written as a dense
+    matrix from its columns (damping per row on every level)."""
+    A = W.diffusion7(5, 1.5, 21)
+    h = O.Hierarchy(A, coarse_size=10, aggr_steps=2)
+    rng = np.random.default_rng(3)
+    for k in range(h.num_levels):
+        h.set_omega(k, 0.6 + 0.8 * rng.random(h.level_n(k)))
+    B = dense_B(h, A.n)
+    E = np.eye(A.n) - A.to_scipy().toarray() @ B
+    r0 = W.random_vector(A.n, 9)
+    ref = np.log(np.linalg.norm(np.linalg.matrix_power(E, m) @ r0) / np.linalg.norm(r0)) / m
+    assert ref < 0.0
+    assert abs(h.loss(r0, m) - ref) < 1e-12
 
 
 def test_unit_omega_reproduces_plain_smoother_bitwise():
