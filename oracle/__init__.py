@@ -2,8 +2,10 @@
 
 TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU-baseline
 leg of the benchmark may import this package; the CUDA library never does and
-shares no code with it.  The arithmetic lives in ``orc.c`` (plain serial FP64
-C); this module compiles it with gcc on first use and marshals numpy arrays.
+shares no code with it.  The arithmetic lives in ``orc.c`` (plain FP64 C);
+this module compiles it with gcc on first use and marshals numpy arrays.  The
+serial build is the checker; the OpenMP build of the same source (``omp=True``)
+is only the timed CPU baseline.
 """
 from __future__ import annotations
 
@@ -18,8 +20,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liborc.so")
+_SO_OMP = os.path.join(_BUILD, "liborc_omp.so")
 _LOCK = threading.Lock()
-_LIB = None
+_LIBS = {}
 
 FP64, FP32, FP32_BF16FINE = 0, 1, 2
 COARSE_L1JACOBI, COARSE_DENSE_CHOL = 0, 1
@@ -27,18 +30,21 @@ PROLONG_UNIT, PROLONG_W_NORMALIZED = 0, 1
 OK, NOT_CONVERGED, ERR_ARG, ERR_BREAKDOWN = 0, 1, -1, -3
 
 
-def build(force: bool = False) -> str:
-    """Compile orc.c into _build/liborc.so (no FMA contraction)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile orc.c into _build/liborc.so (serial, the checker) or, with omp,
+    _build/liborc_omp.so (the same source with its OpenMP row loops on: the
+    timed CPU baseline).  No FMA contraction in either."""
     src = os.path.join(_HERE, "orc.c")
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(
+    so = _SO_OMP if omp else _SO
+    if not force and os.path.exists(so) and os.path.getmtime(so) >= max(
             os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "orc.h"))):
-        return _SO
+        return so
     os.makedirs(_BUILD, exist_ok=True)
-    tmp = _SO + f".{os.getpid()}.tmp"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                           "-o", tmp, src, "-lm"])
-    os.replace(tmp, _SO)
-    return _SO
+    tmp = so + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared"]
+                          + (["-fopenmp"] if omp else []) + ["-o", tmp, src, "-lm"])
+    os.replace(tmp, so)
+    return so
 
 
 class _Params(ctypes.Structure):
@@ -47,11 +53,10 @@ class _Params(ctypes.Structure):
         "coarse_sweeps", "coarse_solver", "precision", "true_res_every", "num_parts", "cycle", "relax_type", "prolong_scale")]
 
 
-def _lib():
-    global _LIB
+def _lib(omp: bool = False):
     with _LOCK:
-        if _LIB is None:
-            lib = ctypes.CDLL(build())
+        if omp not in _LIBS:
+            lib = ctypes.CDLL(build(omp=omp))
             P = ctypes.c_void_p
             i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
             f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
@@ -84,8 +89,14 @@ def _lib():
             lib.orc_vcycle_loss_grad.restype = ctypes.c_double
             lib.orc_round_bf16.argtypes = [ctypes.c_float]
             lib.orc_round_bf16.restype = ctypes.c_float
-            _LIB = lib
-    return _LIB
+            lib.orc_threads.argtypes = []
+            _LIBS[omp] = lib
+    return _LIBS[omp]
+
+
+def threads(omp: bool = True) -> int:
+    """Threads the row loops of the given build use (1 for the serial checker)."""
+    return _lib(omp).orc_threads()
 
 
 def _i32(a):
@@ -160,10 +171,12 @@ class Params:
 class Hierarchy:
     """Oracle AMG hierarchy (Alg. 3 with s-fold composition) plus the solve phase."""
 
-    def __init__(self, A, params: Params | None = None, **kw):
+    def __init__(self, A, params: Params | None = None, omp: bool = False, **kw):
+        """omp: run on the OpenMP build (the timed CPU baseline) instead of the
+        serial checker."""
         self.params = params or Params(**kw)
         rp, ci, v = _i32(A.row_ptr), _i32(A.col_idx), _f64(A.val)
-        self._lib = _lib()
+        self._lib = _lib(omp)
         self._h = self._lib.orc_setup(A.n, rp, ci, v, ctypes.byref(self.params._c()))
         if not self._h:
             raise ValueError("oracle setup rejected the matrix")

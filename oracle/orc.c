@@ -32,6 +32,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAXL 64
 #define ORC_MAXPAIR 256
@@ -285,6 +288,14 @@ int64_t orc_galerkin(int n, const int32_t* rp, const int32_t* ci, const double* 
 /* ------------------------------------------------------------------ */
 /* bf16 round-to-nearest-even of a float (bias-and-truncate method) */
 
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 float orc_round_bf16(float x) {
   uint32_t u;
   memcpy(&u, &x, 4);
@@ -535,6 +546,7 @@ int orc_set_omega(orc_hier* h, int k, const double* omega) {
 
 void orc_spmv(const orc_hier* h, int k, const double* x, double* y) {
   const ocsr* A = &h->A[k];
+  #pragma omp parallel for schedule(static)
   for (int i = 0; i < A->n; ++i) {
     double s = 0.0;
     for (int32_t p = A->rp[i]; p < A->rp[i + 1]; ++p) s += A->v[p] * x[A->ci[p]];
@@ -544,6 +556,7 @@ void orc_spmv(const orc_hier* h, int k, const double* x, double* y) {
 
 /* one l1-Jacobi sweep z <- z + D (r - A z), Jacobi (all rows from the old z) */
 static void sweep_d(const ocsr* A, const double* D, const double* r, double* z, double* tmp) {
+  #pragma omp parallel for schedule(static)
   for (int i = 0; i < A->n; ++i) {
     double s = 0.0;
     for (int32_t p = A->rp[i]; p < A->rp[i + 1]; ++p) s += A->v[p] * z[A->ci[p]];
@@ -572,6 +585,7 @@ static void smooth_from_zero_d(const ocsr* A, const double* D, const double* r, 
     memset(z, 0, sizeof(double) * (size_t)A->n);
     return;
   }
+  #pragma omp parallel for schedule(static)
   for (int i = 0; i < A->n; ++i) z[i] = D[i] * r[i]; /* first sweep from z = 0 */
   for (int s = 1; s < sweeps; ++s) sweep_d(A, D, r, z, tmp);
 }
@@ -592,6 +606,7 @@ static void vcycle_d(orc_hier* h, int k, const double* r, double* z) {
   /* residual, then restriction r_c = P^T (r - A z), members in ascending order */
   double* rc = (double*)xcalloc((size_t)nc, sizeof(double));
   double* zc = (double*)xcalloc((size_t)nc, sizeof(double));
+  #pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) {
     double s = 0.0;
     for (int32_t p = A->rp[i]; p < A->rp[i + 1]; ++p) s += A->v[p] * z[A->ci[p]];
@@ -610,6 +625,7 @@ static void vcycle_d(orc_hier* h, int k, const double* r, double* z) {
     free(rc2);
     free(ec2);
   }
+  #pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) z[i] += zc[agg[i]]; /* prolongation, unit P */
   for (int s = 0; s < h->p.post_sweeps; ++s) sweep_d(A, h->dinv[k], r, z, tmp);
   free(rc);
@@ -623,6 +639,7 @@ static void vcycle_d(orc_hier* h, int k, const double* r, double* z) {
  * takes a float-rounded input */
 
 static void sweep_f(const ocsr* A, const float* val, const float* D, const float* r, float* z, float* tmp) {
+  #pragma omp parallel for schedule(static)
   for (int i = 0; i < A->n; ++i) {
     float s = 0.0f;
     for (int32_t p = A->rp[i]; p < A->rp[i + 1]; ++p) s += val[p] * z[A->ci[p]];
@@ -655,11 +672,13 @@ static void vcycle_f(orc_hier* h, int k, const float* r, float* z) {
   if (h->p.pre_sweeps <= 0) {
     memset(z, 0, sizeof(float) * (size_t)n);
   } else {
+    #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) z[i] = D[i] * r[i];
     for (int s = 1; s < h->p.pre_sweeps; ++s) sweep_f(A, val, D, r, z, tmp);
   }
   float* rc = (float*)xcalloc((size_t)nc, sizeof(float));
   float* zc = (float*)xcalloc((size_t)nc, sizeof(float));
+  #pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) {
     float s = 0.0f;
     for (int32_t p = A->rp[i]; p < A->rp[i + 1]; ++p) s += val[p] * z[A->ci[p]];
@@ -689,6 +708,7 @@ static void vcycle_f(orc_hier* h, int k, const float* r, float* z) {
     free(rc2);
     free(ec2);
   }
+  #pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) z[i] += zc[agg[i]];
   for (int s = 0; s < h->p.post_sweeps; ++s) sweep_f(A, val, D, r, z, tmp);
   free(rc);
@@ -716,12 +736,14 @@ void orc_vcycle(orc_hier* h, const double* r, double* z) {
 
 static double dot(int n, const double* x, const double* y) {
   double s = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : s)
   for (int i = 0; i < n; ++i) s += x[i] * y[i];
   return s;
 }
 
 static void residual(const orc_hier* h, const double* b, const double* u, double* r) {
   orc_spmv(h, 0, u, r);
+  #pragma omp parallel for schedule(static)
   for (int i = 0; i < h->A[0].n; ++i) r[i] = b[i] - r[i];
 }
 
@@ -778,7 +800,9 @@ int orc_fcg(orc_hier* h, const double* b, double* u, double tol, int maxit, int 
       memcpy(d, w, sizeof(double) * (size_t)n);
       memcpy(q, v, sizeof(double) * (size_t)n);
       double a = alpha / rho;
+      #pragma omp parallel for schedule(static)
       for (int i = 0; i < n; ++i) u[i] += a * d[i];
+      #pragma omp parallel for schedule(static)
       for (int i = 0; i < n; ++i) r[i] -= a * q[i];
     } else {
       double beta = dot(n, w, v);
@@ -789,10 +813,14 @@ int orc_fcg(orc_hier* h, const double* b, double* u, double tol, int maxit, int 
         break;
       }
       double g = gamma / rho;
+      #pragma omp parallel for schedule(static)
       for (int i = 0; i < n; ++i) d[i] = w[i] - g * d[i];
+      #pragma omp parallel for schedule(static)
       for (int i = 0; i < n; ++i) q[i] = v[i] - g * q[i];
       double a = alpha / rho_new;
+      #pragma omp parallel for schedule(static)
       for (int i = 0; i < n; ++i) u[i] += a * d[i];
+      #pragma omp parallel for schedule(static)
       for (int i = 0; i < n; ++i) r[i] -= a * q[i];
       rho = rho_new;
     }

@@ -11,6 +11,13 @@
  * coarsening"), the l1-Jacobi smoother (Sec. 3.1) and the experimental
  * settings of Sec. 5 / Listing 1 (4+4 sweeps, 20 coarse sweeps, aggregates of
  * at most 8, coarsest size 40*nd, rtol 1e-6, 1000 iterations).
+ *
+ * The same source is built twice: serially (the checker the tests use; the
+ * OpenMP pragmas are ignored) and with -fopenmp as the timed CPU baseline,
+ * where the row loops of the SpMV, the sweeps, the residuals, the
+ * prolongation, the dot products and the axpys of Alg. 1 are split statically
+ * over the host's cores (the dot products then sum in another order; the
+ * setup and the restriction stay serial).
  */
 #ifndef ORC_H
 #define ORC_H
@@ -83,6 +90,9 @@ void orc_spmv(const orc_hier* h, int k, const double* x, double* y);
  * V-cycle only: NaN for another relaxation or cycle) */
 double orc_vcycle_loss(orc_hier* h, const double* r0, int m);
 double orc_vcycle_loss_grad(orc_hier* h, const double* r0, int m, double* const* domega);
+
+/* threads the row loops use: 1 in the serial build */
+int orc_threads(void);
 
 /* plain helpers for bf16 emulation (used by tests) */
 float orc_round_bf16(float x);

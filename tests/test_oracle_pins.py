@@ -842,3 +842,25 @@ def test_low_precision_vcycle_equals_fp64_in_exact_arithmetic(kw, levels):
         assert np.array_equal(hf.vcycle(r), zd)
         zf = hf.vcycle(rg)
         assert not np.array_equal(zf, zg) and np.linalg.norm(zf - zg) < 1e-6 * np.linalg.norm(zg)
+
+
+# ----------------------------------------------------------------------------
+# the OpenMP build of the oracle (timed CPU baseline only) computes the same solve
+
+
+def test_openmp_build_matches_serial_checker():
+    A = W.diffusion27(14, 2.0, 7)
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 2))
+    ser, par = O.Hierarchy(A), O.Hierarchy(A, omp=True)
+    assert O.threads(omp=False) == 1 and O.threads(omp=True) >= 1
+    for k in range(ser.num_levels - 1):
+        assert np.array_equal(ser.level_agg(k), par.level_agg(k))
+    r = W.random_vector(A.n, 3)
+    zs, zp = ser.vcycle(r), par.vcycle(r)
+    assert np.array_equal(zs, zp)  # row loops only: every row sums in the same order
+    rs, rp_ = ser.fcg(b), par.fcg(b)
+    assert rp_["status"] == O.OK and abs(rs["iters"] - rp_["iters"]) <= 1
+    m = min(rs["iters"], rp_["iters"])
+    xs = ser.fcg(b, tol=0.0, maxit=m)["x"]
+    xp = par.fcg(b, tol=0.0, maxit=m)["x"]
+    assert np.linalg.norm(xs - xp) / np.linalg.norm(xs) < 1e-10  # the dot products sum in another order
