@@ -7,11 +7,15 @@ the whole V-cycle.  One step = one complete solve of the workload from u_0 = 0:
 every FCG iteration (V-cycle, SpMV + dots, axpys, stop test) through the C ABI.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload poisson160] [--precision fp64|fp32|bf16fine]
+                  [--workload poisson320] [--precision fp64|fp32|bf16fine]
+
+The default workload is the largest single-GPU configuration, 7-point Poisson
+320^3 (32.8M rows, 228.8M nonzeros).
 
 Several GPUs run independent replicas (the path has no exchange step on one
 node's worth of work): each rank solves its own copy, the step time is the
-maximum over ranks.  --impl reference times the CPU oracle on the same workload.
+maximum over ranks.  --impl reference times the CPU oracle on the same workload
+(its OpenMP build, on every core of the host).
 """
 from __future__ import annotations
 
@@ -40,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="poisson160")
+    ap.add_argument("--workload", default="poisson320")
     ap.add_argument("--precision", choices=list(PRECISIONS), default="fp64")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -169,23 +173,30 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def csrc_digest() -> str:
+# the sources that define the dominant kernel (the pipelined row kernel and the
+# device helpers it uses); its launch shape on level 0 is checked separately
+KERNEL_SOURCES = ("rows.cuh", "amg_internal.cuh")
+
+
+def kernel_digest() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2303_02352_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload: str, precision: str):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
-    or None when that summary was taken on other kernel sources."""
+def ncu_traffic(workload: str, precision: str, tile_rows: int, stage_scale: int):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu record,
+    or None when that record was taken on other kernel sources or another
+    launch shape (tile height, stage size) of the level-0 kernel."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(f"{workload}:{precision}")
-    if not d or d.get("csrc_digest") != csrc_digest():
+    if not d or d.get("kernel_digest") != kernel_digest():
+        return None
+    if d.get("tile_rows") != tile_rows or d.get("stage_scale") != stage_scale:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -194,13 +205,15 @@ def ncu_traffic(workload: str, precision: str):
 # oracle timing (CPU baseline / reference arm)
 
 def oracle_solve_ms(A, b, precision: str, maxit=1000):
+    """One complete solve of the oracle's OpenMP build (every host core in the
+    affinity mask); returns (solve ms, setup ms, iterations, x, threads)."""
     import oracle as O
     t0 = time.perf_counter()
-    h = O.Hierarchy(A, precision={"fp64": O.FP64, "fp32": O.FP32, "bf16fine": O.FP32_BF16FINE}[precision])
+    h = O.Hierarchy(A, omp=True, precision={"fp64": O.FP64, "fp32": O.FP32, "bf16fine": O.FP32_BF16FINE}[precision])
     t1 = time.perf_counter()
     res = h.fcg(b, maxit=maxit)
     t2 = time.perf_counter()
-    return (t2 - t1) * 1e3, (t1 - t0) * 1e3, res["iters"], res["x"]
+    return (t2 - t1) * 1e3, (t1 - t0) * 1e3, res["iters"], res["x"], O.threads(omp=True)
 
 
 def run_reference(args, rank, world):
@@ -210,7 +223,8 @@ def run_reference(args, rank, world):
     A, b, desc = W.config(args.workload)
     import oracle as O
     prec = {"fp64": O.FP64, "fp32": O.FP32, "bf16fine": O.FP32_BF16FINE}[args.precision]
-    h = O.Hierarchy(A, precision=prec)
+    h = O.Hierarchy(A, precision=prec, omp=True)
+    cores = O.threads(omp=True)
     # the first warm-up step is a complete solve: it fixes the iteration count
     t0 = time.perf_counter()
     full = h.fcg(b, tol=args.tol)
@@ -226,14 +240,16 @@ def run_reference(args, rank, world):
         h.fcg(b, tol=0.0 if sample_it < iters else args.tol, maxit=sample_it)
         times.append((time.perf_counter() - t0) * 1e3 * iters / sample_it)
     ms = sum(times) / len(times)
-    sample = (f"oracle (serial C, FP64) on {desc}: each step one FCG solve to {args.tol:g}"
+    kind = f"oracle (C, OpenMP build, {cores} threads)"
+    sample = (f"{kind} on {desc}: each step one FCG solve to {args.tol:g}, setup excluded"
               if sample_it >= iters else
-              f"oracle (serial C) on {desc}: each step {sample_it} of the {iters} FCG iterations, scaled to {iters}")
+              f"{kind} on {desc}: each step {sample_it} of the {iters} FCG iterations, scaled to {iters}; "
+              f"setup excluded")
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else DTYPE[args.precision],
             "data": "synthetic", "config": {"workload": desc, "precision": args.precision, "iters": full["iters"]},
-            "cpu_baseline": {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -265,10 +281,11 @@ def main():
     cpu = None
     x_oracle = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ms_o, setup_o, it_o, x_oracle = oracle_solve_ms(A, b_np, "fp64")
-        cpu = {"value": ms_o, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one complete oracle solve (serial C, fp64) of {desc} to {args.tol:g}: "
-                         f"{it_o} iterations; oracle setup {setup_o:.0f} ms not included"}
+        ms_o, setup_o, it_o, x_oracle, cores = oracle_solve_ms(A, b_np, "fp64")
+        cpu = {"value": ms_o, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"one complete oracle solve (C, fp64, OpenMP build: row loops of the SpMV, "
+                         f"sweeps, residuals, dots and axpys over {cores} threads) of {desc} to "
+                         f"{args.tol:g}: {it_o} iterations; oracle setup {setup_o:.0f} ms (serial) not included"}
 
     net = None
     if args.learned or not args.no_extra:
@@ -435,7 +452,9 @@ def main():
                        "kernel_forms": {"tile_rows": info["tile_rows"], "stage_scale": info["stage_scale"],
                                         "fused_bottom_from_level": info["bottom_level"]}},
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(ach / peak, 4), "traffic": ncu_traffic(args.workload, args.precision),
+                         "frac": round(ach / peak, 4),
+                         "traffic": ncu_traffic(args.workload, args.precision, info["tile_rows"][0],
+                                                info["stage_scale"][0]),
                          "kernel": "l1-Jacobi sweep, level 0", "algorithmic_bytes_per_launch": by_sweep,
                          "launch_ms": round(t_sweep, 5), "peak_kind": peak_kind},
             "vcycle": {"ms": round(t_vc, 4), "bytes": info["vcycle_bytes"], "GB/s": round(vc_gbs, 1),
