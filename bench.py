@@ -370,9 +370,7 @@ def main():
         kernels[nm] = {"ms": round(t, 5), "GB/s": round(by / (t * 1e-3) / 1e9, 1),
                        "frac": round(by / (t * 1e-3) / 1e9 / peak, 3)}
 
-    batch = g.params["graph_batch"]
-    replays = -(-iters // batch) * batch if iters > 0 else 0
-    launches_per_solve = 1 + replays * info["iteration_launches"]
+    launches_per_solve = g.info()["last_solve_launches"]  # the library counts the launches of its last solve
 
     xs = torch.as_tensor(W.exact_solution(args.workload, n), device="cuda")
     xo = torch.as_tensor(x_oracle, device="cuda") if x_oracle is not None else None
@@ -438,6 +436,15 @@ def main():
             gd.close()
         extras["setup_split_ms"] = {"total": info["setup_ms"], "matching": info["setup_match_ms"],
                                     "galerkin": info["setup_galerkin_ms"]}
+        # w-normalised prolongator values (Sec. 3.1), level matrices by the general
+        # sparse product: solve, and the setup split matching / pairwise Galerkin /
+        # general product
+        gn = amg.Hierarchy(A, precision=PRECISIONS[args.precision], prolong_scale=1)
+        ni = gn.info()
+        extras["w_normalised_prolongator"] = {**timed(gn), "setup_ms": {
+            "total": ni["setup_ms"], "matching": ni["setup_match_ms"], "galerkin_pairwise": ni["setup_galerkin_ms"],
+            "spgemm": ni["setup_spgemm_ms"]}}
+        gn.close()
 
     if rank == 0:
         line = {

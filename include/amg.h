@@ -68,12 +68,18 @@ typedef struct {
   int32_t precision;      /* amg_precision of the hierarchy inside the V-cycle (AMG_FP64) */
   int32_t true_res_every; /* low precision: r <- b - A u every k iterations (50); 0 = never */
   int32_t use_graph;      /* 1: replay the V-cycle and the FCG iteration as CUDA graphs (1) */
-  int32_t graph_batch;    /* FCG iterations launched between two convergence reads (4) */
+  int32_t graph_batch;    /* FCG iterations launched before the first convergence read (4); later reads
+                             follow the observed convergence factor (1: a read after every iteration) */
   int32_t num_parts;      /* decoupled aggregation (Sec. 4.1): match only inside this many
                              contiguous row blocks, as np tasks would (1 = global matching) */
   int32_t cycle;          /* Listing 1 cycle_type: 0 V-cycle, 2 W-cycle (0) */
   int32_t relax_type;     /* Listing 1 relax_type: 4 l1-Jacobi, D = omega / sum_j |a_ij| (4);
                              0 Jacobi, D = omega / a_ii; every level including the coarsest */
+  int32_t prolong_scale;  /* prolongator values (Sec. 3.1: they follow the smooth vector w,
+                             w_next = P^T w): 0 unit entries, P 1 = 1 (0); 1 w-normalised
+                             entries w_i / |w on the aggregate|, P^T P = I, with the level matrices
+                             formed by the general sparse product amg_spgemm (Alg. 4's local
+                             product); the aggregates are the same in both forms */
 } amg_params;
 
 typedef struct {
@@ -93,6 +99,9 @@ typedef struct {
   int32_t bottom_level;       /* first level of the fused bottom (one cluster launch); num_levels: none */
   int32_t tile_rows[40];      /* rows per tile of the level's pipelined row kernels (0: non-pipelined) */
   int32_t stage_scale[40];    /* pipeline stage size of those kernels in units of the standard stage */
+  double setup_spgemm_ms;     /* setup time in the general sparse products (prolong_scale = 1) */
+  int32_t last_solve_launches; /* kernel launches of the last solve on the handle (0 before any) */
+  int32_t consumer_groups[40];  /* groups of consumer warps taking a level's tiles in turn (0: non-pipelined) */
 } amg_info_t;
 
 typedef struct amg_handle amg_handle;
@@ -213,6 +222,15 @@ amg_status amg_adam_step(int32_t np, float* theta, const float* grad, float* m, 
 amg_status amg_apply_mlp(amg_handle* h, const uint16_t* w_bf16);
 amg_status amg_vcycle_backward(amg_handle* h, const double* r, const double* dz, double* dr,
                                double* const* domega);
+/* amg_vcycle_loss: the training loss of the damping, L = (1/m) ln(|r_m| / |r_0|)
+ *   with r_{t+1} = r_t - A B(omega) r_t (m steps of the stationary iteration of
+ *   the FP64 V-cycle on level 0), into *loss (host); with domega not NULL also
+ *   dL/domega for every level k (device, n_k doubles each, overwritten), by the
+ *   adjoint of the m steps (dL/dr_m = r_m / (m |r_m|^2); each step back takes
+ *   dL/dz_t = -A dL/dr_{t+1} through amg_vcycle_backward's adjoint).  r0:
+ *   device, n, not zero.  V-cycle, l1-Jacobi and unit prolongators only
+ *   (AMG_ERR_INVALID_ARG otherwise).  Work buffers are kept by the handle. */
+amg_status amg_vcycle_loss(amg_handle* h, const double* r0, int32_t m, double* loss, double* const* domega);
 
 /*
  * Residual check that allocates nothing (the paper has no counterpart; this is
@@ -235,11 +253,60 @@ amg_status amg_vcycle_backward(amg_handle* h, const double* r, const double* dz,
 amg_status amg_residual_norm_noalloc(const amg_csr* A, const double* b, const double* x, double* r,
                                      double* norms, void* stream);
 
+/*
+ * General sparse matrix product C = A B (Sec. 4.2 / Alg. 4 form every coarse
+ * matrix with such a product; this library uses it for the w-normalised
+ * prolongators, prolong_scale = 1).  A: m x k, B: k x n, device CSR with int32
+ * row pointers and column indices; the columns of every row of B strictly
+ * ascending (A's rows may be in any order).  Two calls on the same inputs:
+ *  1. c_col_idx = c_val = NULL: writes C's row pointers (device, m+1 ints) and
+ *     *nnz_c (host) = the number of entries of C (symbolic phase);
+ *  2. c_row_ptr from call 1, c_col_idx and c_val (device, nnz_c each): writes
+ *     the columns (ascending in every row) and the values (numeric phase).
+ * Every structurally present product is kept (an entry whose products cancel
+ * is stored as 0).  Each entry sums its products in a fixed order (the
+ * results are bitwise reproducible).  Scratch is taken from the stream-ordered
+ * allocator for the call; the call synchronises `stream` before returning.
+ * Errors: AMG_ERR_INVALID_ARG (sizes, NULL pointers; in call 1 also row
+ * pointers not monotone, a column out of range or a row of B not strictly
+ * ascending), AMG_ERR_OOM, AMG_ERR_CUDA; amg_last_error(NULL) describes them.
+ */
+amg_status amg_spgemm(int32_t m, int32_t k, int32_t n, const int32_t* a_row_ptr, const int32_t* a_col_idx,
+                      const double* a_val, const int32_t* b_row_ptr, const int32_t* b_col_idx, const double* b_val,
+                      int32_t* c_row_ptr, int32_t* c_col_idx, double* c_val, int64_t* nnz_c, void* stream);
+
 /* Self-check of the bounded device waits: launches one block that waits on a
  * barrier phase nothing completes, with a limit of limit_us microseconds
  * (1 .. 2,000,000).  Returns AMG_ERR_TIMEOUT when the wait gave up and
  * reported as designed (the expected result), AMG_OK if it did not. */
 amg_status amg_check_bounded_wait(int32_t limit_us, void* stream);
+
+/*
+ * Saving a built hierarchy and loading it back (the paper keeps one setup for
+ * many solves, Sec. 5.2; a file lets it outlive the process).
+ * amg_save: writes the level matrices, aggregation maps, dampings (and for
+ *   prolong_scale = 1 the smooth vectors and prolongator values) of h to the
+ *   file at path (created or replaced).  Errors: AMG_ERR_INVALID_ARG (cannot
+ *   open), AMG_ERR_CUDA (write or device copy failed).
+ * amg_load: builds a handle from such a file without matching or Galerkin
+ *   products; the rest (member lists, diagonals, low-precision copies, kernel
+ *   forms, work vectors, graphs) is derived as in amg_setup, so the handle
+ *   computes bit for bit what the saved one did.  p: NULL = the saved
+ *   parameters; otherwise the solve-phase fields are taken from p (sweeps,
+ *   precision, true_res_every, use_graph, graph_batch, cycle, relax_type) and
+ *   aggr_steps, max_levels, coarse_size, num_parts, prolong_scale must equal
+ *   the saved ones.  stream: as for amg_setup.  The file is checked like a
+ *   caller's matrix (structure, diagonal, finite values, maps in range).
+ *   Errors: AMG_ERR_INVALID_ARG (missing, foreign, truncated or corrupt file,
+ *   mismatching parameters), AMG_ERR_NOT_SPD, AMG_ERR_OOM, AMG_ERR_CUDA;
+ *   amg_last_error(NULL) describes them.
+ */
+amg_status amg_save(const amg_handle* h, const char* path);
+amg_status amg_load(const char* path, const amg_params* p, void* stream, amg_handle** out);
+/* The parameter block stored in a saved hierarchy (host, *out); the start of
+ * a p for amg_load that changes only solve-phase fields.  AMG_ERR_INVALID_ARG
+ * if the file cannot be read as a saved hierarchy. */
+amg_status amg_saved_params(const char* path, amg_params* out);
 
 /* Last error message of the handle (or of the last failed amg_setup if h is NULL). */
 const char* amg_last_error(const amg_handle* h);

@@ -37,7 +37,8 @@ class amg_csr(ctypes.Structure):
 
 
 PARAM_FIELDS = ("aggr_steps", "max_levels", "coarse_size", "pre_sweeps", "post_sweeps", "coarse_sweeps",
-                "precision", "true_res_every", "use_graph", "graph_batch", "num_parts", "cycle", "relax_type")
+                "precision", "true_res_every", "use_graph", "graph_batch", "num_parts", "cycle", "relax_type",
+                "prolong_scale")
 
 
 class amg_params(ctypes.Structure):
@@ -51,7 +52,9 @@ class amg_info_t(ctypes.Structure):
                 ("vcycle_launches", ctypes.c_int32), ("iteration_launches", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("setup_match_ms", ctypes.c_double),
                 ("setup_galerkin_ms", ctypes.c_double), ("bottom_level", ctypes.c_int32),
-                ("tile_rows", ctypes.c_int32 * 40), ("stage_scale", ctypes.c_int32 * 40)]
+                ("tile_rows", ctypes.c_int32 * 40), ("stage_scale", ctypes.c_int32 * 40),
+                ("setup_spgemm_ms", ctypes.c_double), ("last_solve_launches", ctypes.c_int32),
+                ("consumer_groups", ctypes.c_int32 * 40)]
 
 
 _LIB = None
@@ -85,6 +88,7 @@ def load(path: str | None = None):
         "amg_kernel_bytes": (I32, [P, I32, I32, DP]),
         "amg_residual_norm_noalloc": (I32, [ctypes.POINTER(amg_csr), P, P, P, P, P]),
         "amg_check_bounded_wait": (I32, [I32, P]),
+        "amg_spgemm": (I32, [I32, I32, I32, P, P, P, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_int64), P]),
         "amg_features": (I32, [P, I32, P]),
         "amg_set_omega": (I32, [P, I32, P]),
         "amg_mlp_workspace_bytes": (ctypes.c_size_t, [I32]),
@@ -94,6 +98,10 @@ def load(path: str | None = None):
                                 ctypes.c_float, I32, P]),
         "amg_apply_mlp": (I32, [P, P]),
         "amg_vcycle_backward": (I32, [P, P, P, P, P]),
+        "amg_vcycle_loss": (I32, [P, P, I32, DP, P]),
+        "amg_save": (I32, [P, ctypes.c_char_p]),
+        "amg_load": (I32, [ctypes.c_char_p, ctypes.POINTER(amg_params), P, ctypes.POINTER(P)]),
+        "amg_saved_params": (I32, [ctypes.c_char_p, ctypes.POINTER(amg_params)]),
         "amg_last_error": (ctypes.c_char_p, [P]),
         "amg_destroy": (None, [P]),
     }
@@ -161,6 +169,39 @@ class Hierarchy:
         self._h = h
         self.device = dev
 
+    @classmethod
+    def load(cls, path: str, stream=None, **params) -> "Hierarchy":
+        """amg_load: a hierarchy saved with ``save``.  Keyword arguments change
+        solve-phase fields of the saved parameters (sweeps, precision,
+        true_res_every, use_graph, graph_batch, cycle, relax_type)."""
+        import torch
+        lib = load()
+        self = cls.__new__(cls)
+        self._torch, self._lib = torch, lib
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        bpath = os.fsencode(path)
+        p = amg_params()
+        st = lib.amg_saved_params(bpath, ctypes.byref(p))
+        if st != OK:
+            raise AmgError(st, lib.amg_last_error(None).decode())
+        for k, v in params.items():
+            if k not in PARAM_FIELDS:
+                raise KeyError(f"unknown parameter {k}")
+            setattr(p, k, int(v))
+        h = ctypes.c_void_p()
+        st = lib.amg_load(bpath, ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != OK:
+            raise AmgError(st, lib.amg_last_error(None).decode())
+        self._h = h
+        self.params = {f: getattr(p, f) for f in PARAM_FIELDS}
+        self.n = self.info()["n"][0]
+        return self
+
+    def save(self, path: str):
+        """amg_save: writes the hierarchy to a file (``Hierarchy.load`` reads it)."""
+        self._check(self._lib.amg_save(self._h, os.fsencode(path)))
+
     # -- lifetime -----------------------------------------------------------
     def close(self):
         h, self._h = getattr(self, "_h", None), None
@@ -189,7 +230,8 @@ class Hierarchy:
                 "iteration_launches": inf.iteration_launches, "precision": inf.precision,
                 "setup_match_ms": inf.setup_match_ms, "setup_galerkin_ms": inf.setup_galerkin_ms,
                 "bottom_level": inf.bottom_level, "tile_rows": list(inf.tile_rows[:L]),
-                "stage_scale": list(inf.stage_scale[:L])}
+                "stage_scale": list(inf.stage_scale[:L]), "setup_spgemm_ms": inf.setup_spgemm_ms,
+                "last_solve_launches": inf.last_solve_launches, "consumer_groups": list(inf.consumer_groups[:L])}
 
     @property
     def num_levels(self) -> int:
@@ -302,6 +344,19 @@ class Hierarchy:
         self._check(self._lib.amg_vcycle_backward(self._h, _ptr(r), _ptr(dz), _ptr(dr), ptrs))
         return dr, dom
 
+    def vcycle_loss(self, r0, m: int, grad: bool = True):
+        """Training loss (1/m) ln(|r_m| / |r_0|), r_{t+1} = r_t - A B r_t, and, with
+        grad, [dL/domega_k for every level] (device float64) from the library."""
+        t = self._torch
+        r0 = self._vec(r0)
+        loss = ctypes.c_double(0.0)
+        dom, ptrs = None, None
+        if grad:
+            dom = [t.empty(nk, dtype=t.float64, device=self.device) for nk in self.info()["n"]]
+            ptrs = (ctypes.c_void_p * len(dom))(*[_ptr(d) for d in dom])
+        self._check(self._lib.amg_vcycle_loss(self._h, _ptr(r0), int(m), ctypes.byref(loss), ptrs))
+        return loss.value, dom
+
     # -- measurement --------------------------------------------------------
     def time_vcycle(self, reps=20) -> float:
         ms = ctypes.c_double(0.0)
@@ -317,6 +372,30 @@ class Hierarchy:
         b = ctypes.c_double(0.0)
         self._check(self._lib.amg_kernel_bytes(self._h, which, level, ctypes.byref(b)))
         return b.value
+
+
+def spgemm(a_row_ptr, a_col_idx, a_val, b_row_ptr, b_col_idx, b_val, ncols: int, stream=None):
+    """amg_spgemm on device tensors (int32 / float64, contiguous): C = A B with
+    A of len(a_row_ptr) - 1 rows, B of len(b_row_ptr) - 1 rows and ``ncols``
+    columns.  Returns (row_ptr, col_idx, val) of C on the same device."""
+    import torch
+    lib = load()
+    m, k = a_row_ptr.numel() - 1, b_row_ptr.numel() - 1
+    dev = a_row_ptr.device
+    s = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    crp = torch.empty(m + 1, dtype=torch.int32, device=dev)
+    nnz = ctypes.c_int64(0)
+    args = (m, k, int(ncols), _ptr(a_row_ptr), _ptr(a_col_idx), _ptr(a_val), _ptr(b_row_ptr), _ptr(b_col_idx),
+            _ptr(b_val))
+    st = lib.amg_spgemm(*args, _ptr(crp), None, None, ctypes.byref(nnz), s)
+    if st != OK:
+        raise AmgError(st, lib.amg_last_error(None).decode())
+    cci = torch.empty(max(1, nnz.value), dtype=torch.int32, device=dev)
+    cv = torch.empty(max(1, nnz.value), dtype=torch.float64, device=dev)
+    st = lib.amg_spgemm(*args, _ptr(crp), _ptr(cci), _ptr(cv), ctypes.byref(nnz), s)
+    if st != OK:
+        raise AmgError(st, lib.amg_last_error(None).decode())
+    return crp, cci[: nnz.value], cv[: nnz.value]
 
 
 # -- module-level calls (the Python form of amg_setup / amg_pcg_solve) ------

@@ -79,7 +79,7 @@ struct Level {
   int Rd = 256;              // tile height with FP64 values (outer kernels, amg_spmv)
   bool pipe = false;         // every tile fits a pipeline stage (V-cycle value type)
   bool piped = false;        // same with FP64 values
-  int sb = 1;                // stage scale of the pipelined kernels (4: FP64 long rows, one thread per row)
+  int sb = 1;                // stage form of the pipelined kernels (1 standard; 2, 4, 5 FP64 long-row forms; 6 two consumer groups)
   int sbd = 1;               // same for the FP64 outer kernels
   int32_t* rp = nullptr;     // CSR (FP64 values)
   int32_t* ci = nullptr;
@@ -93,6 +93,13 @@ struct Level {
   int32_t* agg = nullptr;    // row -> row of the next level
   int32_t* mptr = nullptr;   // members of each next-level row (ascending)
   int32_t* mem = nullptr;
+  // w-normalised prolongator (prolong_scale = 1): P_{i,agg(i)} = w_i / w^{next}_{agg(i)};
+  // nullptr for the unit prolongator
+  double* wsv = nullptr;     // smooth vector w of this level (w = 1 on level 0)
+  double* pw = nullptr;      // P value of each row (prolongation), n
+  double* pwm = nullptr;     // the same values in member order (restriction), n
+  float* pwf = nullptr;      // float copies for a low-precision level
+  float* pwmf = nullptr;
   bool lowp = false;         // this level runs in float inside the V-cycle
   PairCtl* pctl = nullptr;   // paired-pass kernel state (pair.cuh): control word and per-tile counters
   unsigned* pcnt = nullptr;
@@ -119,6 +126,7 @@ struct amg_handle {
   double setup_ms = 0.0;
   double match_ms = 0.0;      // setup time in the matching steps
   double galerkin_ms = 0.0;   // setup time in the Galerkin products
+  double spgemm_ms = 0.0;     // setup time in the general sparse products (w-normalised prolongator)
   // FCG vectors
   double *b = nullptr, *u = nullptr, *r = nullptr, *w = nullptr, *d = nullptr, *v = nullptr,
          *q = nullptr;
@@ -138,6 +146,7 @@ struct amg_handle {
   int min_tpr = 1;             // tuning hook: least threads per row of the pipelined kernels
   int fuse = 1;                // restriction and prolongation fused into the coarse level's first / last sweep
   int use_big = 0;             // long-row form of the FP64 row kernels: 0 (off; measured best), 4 (4x stages, one thread per row), 2, 5
+  int use_ng = 0;              // 1: levels with tiles of 32-128 rows run two consumer groups with half the threads per row (sb = 6)
   int use_pair = 0;            // consecutive row passes in one launch (0 never: measured slower; 1 on levels with room for the lag; 2 always)
   int pair_slack = -1;         // tiles of lag beyond the halo (-1: two rounds of the grid)
   int kb = AMG_MAXL;           // first level of the fused bottom (nl: none)
@@ -150,6 +159,8 @@ struct amg_handle {
   cudaGraphExec_t g_iter_cg = nullptr;
   int launches_vcycle = 0;
   int launches_iter = 0;
+  int launches_iter_cg = 0;    // kernel launches of one unpreconditioned CG iteration
+  int launches_last_solve = 0; // kernel launches of the last solve
   double bytes_vcycle = 0.0;   // algorithmic bytes of one V-cycle
   double bytes_iter = 0.0;     // algorithmic bytes of one FCG iteration
   AdjState* adj = nullptr;     // allocated by the first amg_vcycle_backward
@@ -206,6 +217,14 @@ static inline int amg_tile_rows(int maxrow, int value_bytes, int rmin = 32) {
 void amg_set_setup_error(const std::string& msg);
 void amg_adj_destroy(amg_handle* h);             // frees the adjoint bookkeeping (learned.cu)  // message for amg_last_error(NULL)
 amg_status amg_level_diag(amg_handle* h, int k);   // l1 norms and D = omega / l1 of level k
+// w-normalised prolongators (spgemm.cu): smooth vectors, P values and the
+// level matrices P^T A P by the general sparse product, from level 0 down
+amg_status amg_normalise_hierarchy(amg_handle* h);
+amg_status amg_build_members(amg_handle* h, int k);  // member lists of level k's aggregates (setup.cu)
+amg_status amg_member_values(amg_handle* h, int k);  // pwm of level k from pw and the member lists (spgemm.cu)
+amg_status amg_finish_setup(amg_handle* h);          // derived data, plan, work vectors, graphs (setup.cu)
+amg_status amg_check_level(amg_handle* h, int k, int nc);  // structure of a level read from a file (setup.cu)
+void amg_read_hooks(amg_handle* h);                  // test and tuning hooks from the environment (setup.cu)
 
 int amg_num_sms();  // multiprocessors of the current device
 

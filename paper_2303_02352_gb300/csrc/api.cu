@@ -25,6 +25,7 @@ extern "C" void amg_params_default(amg_params* p) {
   p->num_parts = 1;
   p->cycle = 0;
   p->relax_type = 4;
+  p->prolong_scale = 0;
 }
 
 extern "C" amg_status amg_info(const amg_handle* h, amg_info_t* info) {
@@ -47,11 +48,14 @@ extern "C" amg_status amg_info(const amg_handle* h, amg_info_t* info) {
   info->precision = h->p.precision;
   info->setup_match_ms = h->match_ms;
   info->setup_galerkin_ms = h->galerkin_ms;
+  info->setup_spgemm_ms = h->spgemm_ms;
+  info->last_solve_launches = h->launches_last_solve;
   info->bottom_level = h->kb < h->nl ? h->kb : h->nl;
   for (int k = 0; k < h->nl && k < 40; ++k) {
     const Level& L = h->L[k];
     info->tile_rows[k] = L.pipe ? L.R : 0;
-    info->stage_scale[k] = L.pipe ? (L.sb == 5 ? 2 : L.sb) : 0;
+    info->stage_scale[k] = L.pipe ? (L.sb == 5 ? 2 : (L.sb == 6 ? 1 : L.sb)) : 0;
+    info->consumer_groups[k] = L.pipe ? ((L.sb == 5 || L.sb == 6) ? 2 : 1) : 0;
   }
   return AMG_OK;
 }

@@ -101,6 +101,25 @@ __device__ __forceinline__ T dget(const BotLevel& L, const Ctx& c, int off, int 
   return cg::this_cluster().map_shared_rank(local, (unsigned)o)[k];
 }
 
+// address of entry j of a distributed vector (own block: the local section;
+// another block: its section through the cluster window).  A select, not a
+// branch, so that a row's loads can all be issued before the first returns.
+template <typename T>
+__device__ __forceinline__ const T* daddr(const BotLevel& L, const Ctx& c, int off, int j) {
+  j = amg_chk(j, L.n);
+  const int o = (int)(((unsigned long long)(unsigned)j * L.magic) >> 32);
+  const T* local = sec<T>(c, off);
+  const T* remote = cg::this_cluster().map_shared_rank(local, (unsigned)o);
+  return (o == c.me ? local : remote) + (j - o * L.chunk);
+}
+
+// gathers of a row issued before its multiply-adds (within the 64 registers a
+// thread of a 1024-thread block has)
+template <typename T>
+__host__ __device__ constexpr int bot_batch() {
+  return sizeof(T) == 8 ? 4 : 8;
+}
+
 // copy this block's slice of level L (and of its maps to the next level C)
 template <typename MT, typename VT>
 __device__ void load_level(const BotLevel& L, const BotLevel* C, const Ctx& c) {
@@ -141,8 +160,18 @@ __device__ __forceinline__ VT row_resid(const BotLevel& L, const Ctx& c, int xo,
   const MT* v = sec<MT>(c, L.o_v);
   VT s = ri;
   const int p1 = rp[i + 1];
-#pragma unroll 4
-  for (int p = rp[i]; p < p1; ++p) s -= (VT)v[p] * dget<VT>(L, c, xo, ci[p]);
+  // the row's gathers (shared or distributed shared memory) are independent:
+  // issue a batch of them, then the multiply-adds in entry order
+  constexpr int B = bot_batch<VT>();
+  for (int p = rp[i]; p < p1; p += B) {
+    VT xv[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (p + u < p1) xv[u] = *daddr<VT>(L, c, xo, ci[p + u]);
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (p + u < p1) s -= (VT)v[p + u] * xv[u];
+  }
   return s;
 }
 
@@ -186,7 +215,17 @@ __device__ __forceinline__ void restrict_to(const BotLevel& L, const BotLevel& C
   CT* rc = sec<CT>(c, C.o_r);
   for (int J = threadIdx.x; J < ccnt; J += blockDim.x) {
     VT s = 0;
-    for (int m = mp[J]; m < mp[J + 1]; ++m) s += dget<VT>(L, c, L.o_t, mm[m]);
+    const int m1 = mp[J + 1];
+    constexpr int B = bot_batch<VT>();
+    for (int m = mp[J]; m < m1; m += B) {  // members' loads first, then the sum in member order
+      VT tv[B];
+#pragma unroll
+      for (int u = 0; u < B; ++u)
+        if (m + u < m1) tv[u] = *daddr<VT>(L, c, L.o_t, mm[m + u]);
+#pragma unroll
+      for (int u = 0; u < B; ++u)
+        if (m + u < m1) s += tv[u];
+    }
     rc[J] = (CT)s;
   }
 }

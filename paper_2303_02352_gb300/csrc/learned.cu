@@ -326,6 +326,10 @@ struct AdjLevel {
 
 struct AdjState {
   AdjLevel L[AMG_MAXL];
+  std::vector<double*> rs;  // residuals r_0 .. r_m of the stationary loss
+  double* lam_r = nullptr;  // dL / d r_t
+  double* lam_z = nullptr;  // dL / d z_t
+  double* scal = nullptr;   // two device doubles: |r|^2 results
 };
 
 void amg_adj_destroy(amg_handle* h) {
@@ -454,6 +458,58 @@ static void ad_backward(amg_handle* h, int k, const double* r, double* lam, doub
 }
 
 // ---------------------------------------------------------------------------
+// training loss of the damping: m steps of the stationary iteration
+// r_{t+1} = r_t - A B(omega) r_t on level 0, L = (1/m) ln(|r_m| / |r_0|)
+
+// out = r - A z (the product summed first, then subtracted)
+__global__ void k_loss_step(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ v, const double* __restrict__ r, const double* __restrict__ z,
+                            double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) s += v[p] * z[ci[p]];
+  out[i] = r[i] - s;
+}
+
+// out = -A x
+__global__ void k_neg_spmv(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const double* __restrict__ v, const double* __restrict__ x, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) s += v[p] * x[ci[p]];
+  out[i] = -s;
+}
+
+// *out = |x|^2 (deterministic: per-block partials in a fixed order)
+__global__ void __launch_bounds__(AMG_BLOCK) k_sqnorm(int n, const double* __restrict__ x, double* partial,
+                                                      unsigned* counter, double* out) {
+  __shared__ double red[32];
+  double acc[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc[0] += x[i] * x[i];
+  if (grid_sum<1>(acc, partial, counter, red) && threadIdx.x == 0) *out = acc[0];
+}
+
+__global__ void k_scale_into(int n, const double* __restrict__ x, double a, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i];
+}
+
+__global__ void k_add_into(int n, const double* __restrict__ x, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += x[i];
+}
+
+static amg_status sqnorm(amg_handle* h, const double* x, double* out_dev) {
+  const int n = h->L[0].n;
+  const int grid = std::max(1, std::min(h->ax_grid, amg_blocks(n)));
+  k_sqnorm<<<grid, AMG_BLOCK, 0, h->stream>>>(n, x, h->partial, h->counter, out_dev);
+  AMG_CK(h, cudaGetLastError());
+  return AMG_OK;
+}
+
+// ---------------------------------------------------------------------------
 // C ABI
 
 extern "C" amg_status amg_features(amg_handle* h, int32_t level, float* feats) {
@@ -549,6 +605,7 @@ extern "C" amg_status amg_vcycle_backward(amg_handle* h, const double* r, const 
     if (!domega[k]) return amg_fail(h, AMG_ERR_INVALID_ARG, "domega[%d] is NULL", k);
   if (h->p.cycle != 0) return amg_fail(h, AMG_ERR_INVALID_ARG, "the adjoint covers the V-cycle only");
   if (h->p.relax_type != 4) return amg_fail(h, AMG_ERR_INVALID_ARG, "the adjoint covers l1-Jacobi only");
+  if (h->p.prolong_scale != 0) return amg_fail(h, AMG_ERR_INVALID_ARG, "the adjoint covers unit prolongators only");
   amg_status st = adj_prepare(h);
   if (st != AMG_OK) return st;
   cudaStream_t s = h->stream;
@@ -560,6 +617,64 @@ extern "C" amg_status amg_vcycle_backward(amg_handle* h, const double* r, const 
   AMG_CK(h, cudaMemcpyAsync(A0.lamA, dz, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   ad_backward(h, 0, r, A0.lamA, domega);
   AMG_CK(h, cudaMemcpyAsync(dr, A0.lr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  AMG_CK(h, cudaGetLastError());
+  AMG_CK(h, cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+extern "C" amg_status amg_vcycle_loss(amg_handle* h, const double* r0, int32_t m, double* loss,
+                                      double* const* domega) {
+  if (!h) return AMG_ERR_INVALID_ARG;
+  if (!r0 || !loss || m < 1) return amg_fail(h, AMG_ERR_INVALID_ARG, "NULL pointer or m < 1");
+  if (domega)
+    for (int k = 0; k < h->nl; ++k)
+      if (!domega[k]) return amg_fail(h, AMG_ERR_INVALID_ARG, "domega[%d] is NULL", k);
+  if (h->p.cycle != 0) return amg_fail(h, AMG_ERR_INVALID_ARG, "the loss covers the V-cycle only");
+  if (domega && h->p.relax_type != 4) return amg_fail(h, AMG_ERR_INVALID_ARG, "the adjoint covers l1-Jacobi only");
+  if (h->p.prolong_scale != 0) return amg_fail(h, AMG_ERR_INVALID_ARG, "the loss covers unit prolongators only");
+  amg_status st = adj_prepare(h);
+  if (st != AMG_OK) return st;
+  AdjState& S = *h->adj;
+  const Level& L0 = h->L[0];
+  const int n = L0.n, nb = amg_blocks(n);
+  cudaStream_t s = h->stream;
+  while ((int)S.rs.size() < m + 1) {
+    double* p = nullptr;
+    AMG_ALLOC(h, p, double, n);
+    S.rs.push_back(p);
+  }
+  if (!S.lam_r) {
+    AMG_ALLOC(h, S.lam_r, double, n);
+    AMG_ALLOC(h, S.lam_z, double, n);
+    AMG_ALLOC(h, S.scal, double, 2);
+  }
+  AdjLevel& A0 = h->adj->L[0];
+  double* z = A0.lamB;  // forward output (the adjoint's buffers are free during the forward steps)
+  AMG_CK(h, cudaMemcpyAsync(S.rs[0], r0, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  for (int t = 0; t < m; ++t) {
+    ad_forward(h, 0, S.rs[t], z);
+    k_loss_step<<<nb, AMG_BLOCK, 0, s>>>(n, L0.rp, L0.ci, L0.v, S.rs[t], z, S.rs[t + 1]);
+  }
+  st = sqnorm(h, S.rs[0], S.scal);
+  if (st != AMG_OK) return st;
+  st = sqnorm(h, S.rs[m], S.scal + 1);
+  if (st != AMG_OK) return st;
+  double nrm[2] = {0.0, 0.0};
+  AMG_CK(h, cudaMemcpyAsync(nrm, S.scal, sizeof(nrm), cudaMemcpyDeviceToHost, s));
+  AMG_CK(h, cudaStreamSynchronize(s));
+  if (!(nrm[0] > 0.0) || !(nrm[1] > 0.0)) return amg_fail(h, AMG_ERR_INVALID_ARG, "|r_0| or |r_m| is zero");
+  *loss = (std::log(std::sqrt(nrm[1])) - std::log(std::sqrt(nrm[0]))) / m;
+  if (!domega) return AMG_OK;
+  // backward: dL/dr_m = r_m / (m |r_m|^2); r_{t+1} = r_t - A z_t gives
+  // dL/dz_t = -A^T dL/dr_{t+1} (A symmetric) and dL/dr_t = dL/dr_{t+1} + B^T dL/dz_t
+  for (int k = 0; k < h->nl; ++k) AMG_CK(h, cudaMemsetAsync(domega[k], 0, sizeof(double) * h->L[k].n, s));
+  k_scale_into<<<nb, AMG_BLOCK, 0, s>>>(n, S.rs[m], 1.0 / ((double)m * nrm[1]), S.lam_r);
+  for (int t = m - 1; t >= 0; --t) {
+    k_neg_spmv<<<nb, AMG_BLOCK, 0, s>>>(n, L0.rp, L0.ci, L0.v, S.lam_r, A0.lamA);
+    ad_forward(h, 0, S.rs[t], S.lam_z);  // re-records the V-cycle of step t (lamA is not touched)
+    ad_backward(h, 0, S.rs[t], A0.lamA, domega);
+    k_add_into<<<nb, AMG_BLOCK, 0, s>>>(n, A0.lr, S.lam_r);
+  }
   AMG_CK(h, cudaGetLastError());
   AMG_CK(h, cudaStreamSynchronize(s));
   return AMG_OK;

@@ -354,6 +354,12 @@ static void scan_exclusive(cudaStream_t s, int n, const int32_t* in, int32_t* ou
   if (n > 0) k_scan_add<<<amg_blocks(n), AMG_BLOCK, 0, s>>>(n, out, scratch);
 }
 
+// the same scan for the other translation units (the general sparse product)
+void amg_scan_exclusive(cudaStream_t s, int n, const int32_t* in, int32_t* out, int32_t* scratch, int32_t* total) {
+  scan_exclusive(s, n, in, out, scratch, total);
+}
+int amg_scan_scratch_ints(int n) { return n / SCAN_TILE + 2; }
+
 __global__ void k_number(int n, const int32_t* __restrict__ mate, const int32_t* __restrict__ opener,
                          const int32_t* __restrict__ pos, int32_t* __restrict__ agg, int32_t* __restrict__ open_idx) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -658,6 +664,31 @@ static amg_status build_members(amg_handle* h, Level& L, int nc) {
   return AMG_OK;
 }
 
+amg_status amg_build_members(amg_handle* h, int k) { return build_members(h, h->L[k], h->L[k + 1].n); }
+
+// aggregation map entries in [0, nc)
+__global__ void k_check_agg(int n, const int32_t* __restrict__ agg, int nc, int* flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && (agg[i] < 0 || agg[i] >= nc)) atomicOr(flags, ST_BADCOL);
+}
+
+// structure of level k as for a caller's matrix (row pointers, columns in
+// range and ascending, diagonal stored and positive, finite values) and its
+// aggregation map in range of the next level's nc rows (nc = 0: no map)
+amg_status amg_check_level(amg_handle* h, int k, int nc) {
+  Level& L = h->L[k];
+  cudaStream_t s = h->stream;
+  int32_t* diagpos;
+  AMG_ALLOC(h, diagpos, int32_t, L.n);
+  AMG_CK(h, cudaMemsetAsync(h->dev_flags, 0, sizeof(int), s));
+  k_validate<<<amg_blocks(L.n), AMG_BLOCK, 0, s>>>(L.n, (int)L.nnz, L.rp, L.ci, L.v, diagpos, h->dev_flags);
+  amg_status st = check_flags(h, "amg_load");
+  amg_release(h, diagpos);
+  if (st != AMG_OK || nc <= 0 || !L.agg) return st;
+  k_check_agg<<<amg_blocks(L.n), AMG_BLOCK, 0, s>>>(L.n, L.agg, nc, h->dev_flags);
+  return check_flags(h, "amg_load: aggregation map");
+}
+
 amg_status amg_level_diag(amg_handle* h, int k) {
   Level& L = h->L[k];
   k_l1<<<amg_blocks(L.n), AMG_BLOCK, 0, h->stream>>>(L.n, L.rp, L.ci, L.v, L.omega, L.l1, L.dinv, L.dinvf,
@@ -693,6 +724,8 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
     return amg_fail(h, AMG_ERR_INVALID_ARG, "row_ptr[0] must be 0 and row_ptr[n] must equal nnz");
   if (h->p.relax_type != 0 && h->p.relax_type != 4)
     return amg_fail(h, AMG_ERR_INVALID_ARG, "relax_type must be 4 (l1-Jacobi) or 0 (Jacobi)");
+  if (h->p.prolong_scale != 0 && h->p.prolong_scale != 1)
+    return amg_fail(h, AMG_ERR_INVALID_ARG, "prolong_scale must be 0 (unit) or 1 (w-normalised)");
   {
     int32_t* diagpos;
     AMG_ALLOC(h, diagpos, int32_t, n);
@@ -723,7 +756,9 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
     std::vector<int32_t> hb(np + 1);
     for (int q = 0; q <= np; ++q) hb[q] = (int32_t)(((int64_t)q * n) / np);
     AMG_ALLOC(h, bnd, int32_t, np + 1);
-    AMG_CK(h, cudaMemcpy(bnd, hb.data(), sizeof(int32_t) * (np + 1), cudaMemcpyHostToDevice));
+    // on the handle's stream, after the allocation's zero fill; hb must outlive the copy
+    AMG_CK(h, cudaMemcpyAsync(bnd, hb.data(), sizeof(int32_t) * (np + 1), cudaMemcpyHostToDevice, s));
+    AMG_CK(h, cudaStreamSynchronize(s));
   }
   while (cur.n > cs && h->nl < maxl) {
     int32_t *agg, *open_idx, *mate;
@@ -792,6 +827,25 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
     amg_release(h, comp);
   }
 
+  // w-normalised prolongators: level matrices by the general sparse product
+  if (h->p.prolong_scale == 1 && h->nl > 1) {
+    AMG_CK(h, cudaStreamSynchronize(s));
+    auto t0 = std::chrono::steady_clock::now();
+    amg_status st = amg_normalise_hierarchy(h);
+    if (st != AMG_OK) return st;
+    AMG_CK(h, cudaStreamSynchronize(s));
+    h->spgemm_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+
+  return amg_finish_setup(h);
+}
+
+// Everything a solve needs beyond the level matrices and aggregation maps:
+// member lists, tile heights, l1 diagonals and D, low-precision copies, the
+// fused-bottom plan, work vectors and graphs.  Shared by amg_setup and
+// amg_load (checkpoint.cu).
+amg_status amg_finish_setup(amg_handle* h) {
+  cudaStream_t s = h->stream;
   // per-level smoother data, members lists and low-precision copies
   const bool lowp = h->p.precision != AMG_FP64 && h->nl > 1;
   for (int k = 0; k < h->nl; ++k) {
@@ -862,6 +916,9 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
       L.Rd = rbig;
       L.sbd = sbig;
     }
+    // two consumer groups with half the threads per row (tiles of 32-128 rows)
+    if (h->use_ng && L.pipe && L.sb == 1 && L.R >= 32 && L.R <= 128) L.sb = 6;
+    if (h->use_ng && L.piped && L.sbd == 1 && L.Rd >= 32 && L.Rd <= 128) L.sbd = 6;
     AMG_ALLOC(h, L.l1, double, L.n);
     AMG_ALLOC(h, L.dinv, double, L.n);
     if (L.lowp) {
@@ -871,10 +928,16 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
       else AMG_ALLOC(h, L.vf, float, L.nnz);
       if (L.nnz)
         k_round_vals<<<amg_blocks(L.nnz), AMG_BLOCK, 0, s>>>(L.nnz, L.v, bfine ? nullptr : L.vf, bfine ? L.vb : nullptr);
+      if (L.pw) {  // prolongator values of a float level
+        AMG_ALLOC(h, L.pwf, float, L.n);
+        AMG_ALLOC(h, L.pwmf, float, L.n);
+        k_round_vals<<<amg_blocks(L.n), AMG_BLOCK, 0, s>>>(L.n, L.pw, L.pwf, nullptr);
+        k_round_vals<<<amg_blocks(L.n), AMG_BLOCK, 0, s>>>(L.n, L.pwm, L.pwmf, nullptr);
+      }
     }
     amg_status st = amg_level_diag(h, k);
     if (st != AMG_OK) return st;
-    if (k < h->nl - 1) {
+    if (k < h->nl - 1 && !L.mptr) {
       st = build_members(h, L, h->L[k + 1].n);
       if (st != AMG_OK) return st;
     }
@@ -884,23 +947,15 @@ static amg_status setup_impl(amg_handle* h, const amg_csr* A) {
     return amg_fail(h, AMG_ERR_INVALID_ARG, "cycle must be 0 (V) or 2 (W)");
   AMG_CK(h, cudaStreamSynchronize(s));
   AMG_CK(h, cudaGetLastError());
-  if (h->use_bottom && h->p.cycle == 0) {  // the small levels in one cluster launch
+  // the small levels in one cluster launch (unit prolongators only)
+  if (h->use_bottom && h->p.cycle == 0 && h->p.prolong_scale == 0) {
     amg_status st = amg_plan_bottom(h);
     if (st != AMG_OK) return st;
   }
   return amg_prepare_solve(h);
 }
 
-extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* stream, amg_handle** out) {
-  if (!out) return AMG_ERR_INVALID_ARG;
-  *out = nullptr;
-  if (!A || A->n <= 0 || A->nnz < A->n || !A->row_ptr || !A->col_idx || !A->val)
-    return AMG_ERR_INVALID_ARG;
-  auto t0 = std::chrono::steady_clock::now();
-  amg_handle* h = new amg_handle();
-  if (p) h->p = *p;
-  else amg_params_default(&h->p);
-  h->stream = (cudaStream_t)stream;
+void amg_read_hooks(amg_handle* h) {
   // test and tuning hooks (environment): AMG_PIPE=0 non-pipelined row kernels,
   // AMG_BOTTOM=0/1/2 bottom levels as separate
   // launches / in one cluster launch / by the owner-spread rule (default),
@@ -921,6 +976,20 @@ extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* str
   if (const char* e = getenv("AMG_PAIR_SLACK")) h->pair_slack = atoi(e);
   if (const char* e = getenv("AMG_FAIL_ALLOC_AFTER")) h->fail_alloc_after = atoi(e);
   if (const char* e = getenv("AMG_PIPE")) h->use_pipe = atoi(e);
+  if (const char* e = getenv("AMG_NG")) h->use_ng = atoi(e);
+}
+
+extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* stream, amg_handle** out) {
+  if (!out) return AMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!A || A->n <= 0 || A->nnz < A->n || !A->row_ptr || !A->col_idx || !A->val)
+    return AMG_ERR_INVALID_ARG;
+  auto t0 = std::chrono::steady_clock::now();
+  amg_handle* h = new amg_handle();
+  if (p) h->p = *p;
+  else amg_params_default(&h->p);
+  h->stream = (cudaStream_t)stream;
+  amg_read_hooks(h);
   amg_status st = setup_impl(h, A);
   if (st != AMG_OK) {
     amg_set_setup_error(h->err);

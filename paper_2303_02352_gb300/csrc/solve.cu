@@ -9,6 +9,7 @@
 // set: the FCG iteration is replayed as a CUDA graph in batches and the
 // iterations after convergence cost one flag read per kernel.
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 
@@ -165,17 +166,22 @@ __global__ void __launch_bounds__(R) k_spmv(int n, const int32_t* __restrict__ r
 // r_c[J] = sum over the members i of aggregate J (ascending) of t_i (one
 // coarse row per thread: the member loads of a row depend on each other, so
 // more rows per thread would only serialise them)
+// (pwm: the prolongator's values in member order for a non-unit prolongator,
+// r_c[J] = sum_i p_i t_i; nullptr for the unit one)
 template <typename VT, typename CT>
 __global__ void __launch_bounds__(AMG_BLOCK) k_restrict(int nc, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
                                                         const VT* __restrict__ t, CT* __restrict__ rc, const int* skip,
-                                                        int n) {
+                                                        int n, const VT* __restrict__ pwm) {
   pdl_trigger();
   pdl_wait();
   if (*skip) return;
   const int J = blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= nc) return;
   VT s = 0;
-  for (int m = mptr[J]; m < mptr[J + 1]; ++m) s += t[amg_chk(mem[m], n)];
+  if (pwm)
+    for (int m = mptr[J]; m < mptr[J + 1]; ++m) s += pwm[m] * t[amg_chk(mem[m], n)];
+  else
+    for (int m = mptr[J]; m < mptr[J + 1]; ++m) s += t[amg_chk(mem[m], n)];
   rc[J] = (CT)s;
 }
 
@@ -186,43 +192,63 @@ template <typename VT, typename CT>
 __global__ void __launch_bounds__(AMG_BLOCK) k_restrict_first(int nc, const int32_t* __restrict__ mptr,
                                                               const int32_t* __restrict__ mem, const VT* __restrict__ t,
                                                               const CT* __restrict__ dinv_c, CT* __restrict__ rc,
-                                                              CT* __restrict__ zc, const int* skip, int n) {
+                                                              CT* __restrict__ zc, const int* skip, int n,
+                                                              const VT* __restrict__ pwm) {
   pdl_trigger();
   pdl_wait();
   if (*skip) return;
   const int J = blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= nc) return;
   VT s = 0;
-  for (int m = mptr[J]; m < mptr[J + 1]; ++m) s += t[amg_chk(mem[m], n)];
+  if (pwm)
+    for (int m = mptr[J]; m < mptr[J + 1]; ++m) s += pwm[m] * t[amg_chk(mem[m], n)];
+  else
+    for (int m = mptr[J]; m < mptr[J + 1]; ++m) s += t[amg_chk(mem[m], n)];
   const CT r = (CT)s;
   rc[J] = r;
   zc[J] = dinv_c[J] * r;
 }
 
-// z_i += z_c[agg(i)]  (unit piecewise-constant prolongator)
+// z_i += z_c[agg(i)]  (unit piecewise-constant prolongator), or
+// z_i += p_i z_c[agg(i)] with the prolongator's values pw (nullptr: unit)
 template <typename VT, typename CT>
 __global__ void __launch_bounds__(AMG_BLOCK) k_prolong(int n, const int32_t* __restrict__ agg, const CT* __restrict__ zc,
-                                                       VT* __restrict__ z, const int* skip, int nc) {
+                                                       VT* __restrict__ z, const int* skip, int nc,
+                                                       const VT* __restrict__ pw) {
   pdl_trigger();
   pdl_wait();
   if (*skip) return;
   const int T = gridDim.x * blockDim.x, i0 = blockIdx.x * blockDim.x + threadIdx.x;
   int a[EW];
-  VT zz[EW];
+  VT zz[EW], pp[EW];
 #pragma unroll
   for (int u = 0; u < EW; ++u) {
     const int i = i0 + u * T;
     a[u] = 0;
+    pp[u] = 1;
     if (i < n) {
       a[u] = agg[i];
       zz[u] = z[i];
+      if (pw) pp[u] = pw[i];
     }
   }
 #pragma unroll
   for (int u = 0; u < EW; ++u) {
     const int i = i0 + u * T;
-    if (i < n) z[i] = zz[u] + (VT)zc[amg_chk(a[u], nc)];
+    if (i < n) z[i] = pw ? zz[u] + pp[u] * (VT)zc[amg_chk(a[u], nc)] : zz[u] + (VT)zc[amg_chk(a[u], nc)];
   }
+}
+
+// prolongator values of a level in the level's vector type (nullptr: unit)
+template <typename VT>
+static const VT* pw_of(const Level& L) {
+  if constexpr (sizeof(VT) == 8) return (const VT*)L.pw;
+  else return (const VT*)L.pwf;
+}
+template <typename VT>
+static const VT* pwm_of(const Level& L) {
+  if constexpr (sizeof(VT) == 8) return (const VT*)L.pwm;
+  else return (const VT*)L.pwmf;
 }
 
 template <typename VT, typename OT>
@@ -502,11 +528,27 @@ int amg_num_sms() {
     default: { constexpr int TP = 32; CALL; } break;    \
   }
 
+// sb = 6 (any value type, tiles of R = 128, 64 or 32 rows): two consumer
+// groups of 128 threads take the tiles in turn from four standard stages, each
+// with half the threads per row of the standard form (1, 2, 4 for R = 128,
+// 64, 32).  Fewer shuffle reductions and fewer idle lanes per row, where the
+// FP64 issue rate limits the standard form; half the resident blocks.
+#define DISPATCH_NG(RR, CALL)                                  \
+  switch (RR) {                                                \
+    case 128: { constexpr int TP = 1; CALL; } break;           \
+    case 64: { constexpr int TP = 2; CALL; } break;            \
+    default: { constexpr int TP = 4; CALL; } break;            \
+  }
+
 // sb = 2 / 4: FP64 level with long rows in 2x / 4x stages (R = 128 with two
 // threads per row / R = 256 with one); sb = 5: two consumer groups taking
 // tiles in turn, R = 128 rows with one thread per row, four 2x stages
 template <int MODE, typename MT, typename VT, typename OT>
 static void launch_rows(cudaStream_t s, int R, int sb, const RowArgs<MT, VT, OT>& a) {
+  if (sb == 6) {
+    DISPATCH_NG(R, (launch_pipe<TP, 4, MODE, MT, VT, OT, 1, 2>(s, a)));
+    return;
+  }
   if constexpr (sizeof(MT) == 8) {
     if (sb == 5) {
       launch_pipe<1, 4, MODE, MT, VT, OT, 2, 2>(s, a);
@@ -540,6 +582,11 @@ static void launch_sweep(cudaStream_t s, const Level& L, const MT* vals, const V
 // grid of the pipelined row kernel of `MODE` on a level with tiles of R rows
 template <int MODE, typename MT, typename VT, typename OT>
 static int rows_grid(int R, int sb, int n) {
+  if (sb == 6) {
+    int g = 0;
+    DISPATCH_NG(R, (g = pipe_grid<TP, 4, MODE, MT, VT, OT, 1, 2>(n)));
+    return g;
+  }
   if constexpr (sizeof(MT) == 8) {
     if (sb == 5) return pipe_grid<1, 4, MODE, MT, VT, OT, 2, 2>(n);
     if (sb == 4) return pipe_grid<1, 2, MODE, MT, VT, OT, 4>(n);
@@ -558,7 +605,7 @@ static int rows_grid(int R, int sb, int n) {
 template <typename MT, typename VT>
 static bool launch_sweep_prolong(cudaStream_t s, const Level& C, const MT* vals, const VT* dinv, const VT* r, const VT* z,
                                  VT* out, const int* skip, int* flags, const Level& F, void* zf, bool any_size = false) {
-  if (!C.pipe) return false;
+  if (!C.pipe || F.pw) return false;  // unit prolongators only
   const int tiles = (C.n + C.R - 1) / C.R;
   if (!any_size && rows_grid<PM_SWEEP_PROLONG, MT, VT, VT>(C.R, C.sb, C.n) < tiles) return false;
   RowArgs<MT, VT, VT> a{C.n, C.rp, C.ci, vals, z, dinv, r, nullptr, nullptr, out, skip, nullptr, nullptr, nullptr, flags,
@@ -844,13 +891,14 @@ amg_status amg_plan_bottom(amg_handle* h) {
   for (int k = k0; k < h->nl; ++k) {
     const Level& L = h->L[k];
     rps[k - k0].resize(L.n + 1);
-    AMG_CK(h, cudaMemcpy(rps[k - k0].data(), L.rp, 4ull * (L.n + 1), cudaMemcpyDeviceToHost));
+    AMG_CK(h, cudaMemcpyAsync(rps[k - k0].data(), L.rp, 4ull * (L.n + 1), cudaMemcpyDeviceToHost, h->stream));
     if (k < h->nl - 1) {
       const int nc = h->L[k + 1].n;
       mps[k - k0].resize(nc + 1);
-      AMG_CK(h, cudaMemcpy(mps[k - k0].data(), L.mptr, 4ull * (nc + 1), cudaMemcpyDeviceToHost));
+      AMG_CK(h, cudaMemcpyAsync(mps[k - k0].data(), L.mptr, 4ull * (nc + 1), cudaMemcpyDeviceToHost, h->stream));
     }
   }
+  AMG_CK(h, cudaStreamSynchronize(h->stream));
   for (int kb = k0; kb < h->nl; ++kb) {
     std::vector<std::vector<int32_t>> r(rps.begin() + (kb - k0), rps.end()), m(mps.begin() + (kb - k0), mps.end());
     for (int cs : {16, 8}) {
@@ -863,7 +911,8 @@ amg_status amg_plan_bottom(amg_handle* h) {
         for (int k = kb; k < h->nl; ++k) {
           const Level& L = h->L[k];
           std::vector<int32_t> ci(L.nnz);
-          AMG_CK(h, cudaMemcpy(ci.data(), L.ci, 4ull * L.nnz, cudaMemcpyDeviceToHost));
+          AMG_CK(h, cudaMemcpyAsync(ci.data(), L.ci, 4ull * L.nnz, cudaMemcpyDeviceToHost, h->stream));
+          AMG_CK(h, cudaStreamSynchronize(h->stream));
           if (owner_spread(rps[k - k0], ci, L.n, (L.n + cs - 1) / cs) > 1.5) return AMG_OK;
         }
       }
@@ -918,20 +967,21 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
   Level& C = h->L[k + 1];
   const int ncb = amg_blocks(C.n);
   const double sx = sizeof(VT), n = L.n, nc = C.n;
+  const double wb = L.pw ? sx * n : 0.0;  // prolongator values read by a non-unit restriction / prolongation
   if (k + 1 == h->kb) {  // the bottom levels in one launch
     const double sc = vec_bytes(C);
     if (k + 1 == h->nl - 1) {
-      amg_launch(k_restrict<VT, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (double*)C.r, R.skip, L.n);
-      R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 8.0 * nc);
+      amg_launch(k_restrict<VT, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (double*)C.r, R.skip, L.n, pwm_of<VT>(L));
+      R.add(wb + 4.0 * (nc + 1) + 4.0 * n + sx * n + 8.0 * nc);
       rec_bottom(R);
-      amg_launch(k_prolong<VT, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, (const double*)C.za, z, R.skip, C.n);
+      amg_launch(k_prolong<VT, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, (const double*)C.za, z, R.skip, C.n, pw_of<VT>(L));
     } else {
-      amg_launch(k_restrict<VT, VT>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip, L.n);
-      R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc);
+      amg_launch(k_restrict<VT, VT>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip, L.n, pwm_of<VT>(L));
+      R.add(wb + 4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc);
       rec_bottom(R);
-      amg_launch(k_prolong<VT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, (const VT*)C.za, z, R.skip, C.n);
+      amg_launch(k_prolong<VT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, (const VT*)C.za, z, R.skip, C.n, pw_of<VT>(L));
     }
-    R.add(4.0 * n + sc * nc + 2.0 * sx * n);
+    R.add(wb + 4.0 * n + sc * nc + 2.0 * sx * n);
     return;
   }
   const bool wcyc = h->p.cycle == 2;
@@ -943,11 +993,11 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
     const bool fr = fuse && h->p.coarse_sweeps > 0;
     if (fr) {
       amg_launch(k_restrict_first<VT, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t,
-                 (const double*)C.dinv, (double*)C.r, (double*)C.za, R.skip, L.n);
-      R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 24.0 * nc);
+                 (const double*)C.dinv, (double*)C.r, (double*)C.za, R.skip, L.n, pwm_of<VT>(L));
+      R.add(wb + 4.0 * (nc + 1) + 4.0 * n + sx * n + 24.0 * nc);
     } else {
-      amg_launch(k_restrict<VT, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (double*)C.r, R.skip, L.n);
-      R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 8.0 * nc);
+      amg_launch(k_restrict<VT, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (double*)C.r, R.skip, L.n, pwm_of<VT>(L));
+      R.add(wb + 4.0 * (nc + 1) + 4.0 * n + sx * n + 8.0 * nc);
     }
     double* zc = rec_coarse(R, k + 1, (const double*)C.r, nullptr, fr, fuse ? &pro : nullptr);
     if (wcyc) {  // W-cycle: e = z_c;  r2 = r_c - A_c e;  e += B_c r2
@@ -963,8 +1013,8 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
       zc = e;
     }
     if (!pro.done) {
-      amg_launch(k_prolong<VT, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip, C.n);
-      R.add(4.0 * n + 8.0 * nc + 2.0 * sx * n);
+      amg_launch(k_prolong<VT, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip, C.n, pw_of<VT>(L));
+      R.add(wb + 4.0 * n + 8.0 * nc + 2.0 * sx * n);
     }
   } else {
     const double sc = vec_bytes(C);
@@ -972,11 +1022,11 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
     if (fr) {
       const VT* dc = C.lowp ? (const VT*)C.dinvf : (const VT*)C.dinv;
       amg_launch(k_restrict_first<VT, VT>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, dc,
-                 (VT*)C.r, (VT*)C.za, R.skip, L.n);
-      R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + 3.0 * sc * nc);
+                 (VT*)C.r, (VT*)C.za, R.skip, L.n, pwm_of<VT>(L));
+      R.add(wb + 4.0 * (nc + 1) + 4.0 * n + sx * n + 3.0 * sc * nc);
     } else {
-      amg_launch(k_restrict<VT, VT>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip, L.n);
-      R.add(4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc);
+      amg_launch(k_restrict<VT, VT>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, L.mptr, L.mem, t, (VT*)C.r, R.skip, L.n, pwm_of<VT>(L));
+      R.add(wb + 4.0 * (nc + 1) + 4.0 * n + sx * n + sc * nc);
     }
     Prol* pp = fuse ? &pro : nullptr;
     VT* zc;
@@ -1000,8 +1050,8 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
       zc = e;
     }
     if (!pro.done) {
-      amg_launch(k_prolong<VT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip, C.n);
-      R.add(4.0 * n + sc * nc + 2.0 * sx * n);
+      amg_launch(k_prolong<VT, VT>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, R.s, L.n, L.agg, zc, z, R.skip, C.n, pw_of<VT>(L));
+      R.add(wb + 4.0 * n + sc * nc + 2.0 * sx * n);
     }
   }
 }
@@ -1265,7 +1315,7 @@ amg_status amg_capture_graphs(amg_handle* h) {
   if (st != AMG_OK) return st;
   st = capture([&](VRec& R) { record_iteration(R, true); }, &h->g_iter, &h->launches_iter, &h->bytes_iter);
   if (st != AMG_OK) return st;
-  st = capture([&](VRec& R) { record_iteration(R, false); }, &h->g_iter_cg, nullptr, nullptr);
+  st = capture([&](VRec& R) { record_iteration(R, false); }, &h->g_iter_cg, &h->launches_iter_cg, nullptr);
   if (st != AMG_OK) return st;
   AMG_CK(h, cudaGetLastError());
   return AMG_OK;
@@ -1365,10 +1415,20 @@ static amg_status run_fcg(amg_handle* h, bool precond, double tol, int maxit, in
   const int g = h->red_grid;
   launch_fcg_resid<RES_INIT>(h, s);
   AMG_CK(h, cudaGetLastError());
+  int launches = 1;
   AMG_CK(h, cudaMemcpyAsync(hs, h->st, sizeof(FcgState), cudaMemcpyDeviceToHost, s));
   AMG_CK(h, cudaStreamSynchronize(s));
   if (hs->nb == 0.0) AMG_CK(h, cudaMemsetAsync(h->u, 0, sizeof(double) * (size_t)n, s));
-  const int batch = std::max(1, h->p.graph_batch);
+  // Convergence reads: the first after graph_batch iterations, each later one
+  // after as many iterations as the convergence factor observed since the
+  // previous read predicts are still needed (at most 64, and not past maxit).
+  // Iterations launched after the stop return at once but still cost their
+  // launches; a short prediction only costs one more read.  graph_batch = 1
+  // reads after every iteration.  The iterations themselves do not depend on
+  // this spacing.
+  int batch = std::max(1, h->p.graph_batch);
+  double res_prev = hs->res;
+  int it_prev = hs->it;
   while (!hs->done) {
     for (int j = 0; j < batch; ++j) {
       if (h->p.use_graph) {
@@ -1378,15 +1438,28 @@ static amg_status run_fcg(amg_handle* h, bool precond, double tol, int maxit, in
         record_iteration(R, precond);
         AMG_CK(h, cudaGetLastError());
       }
+      launches += precond ? h->launches_iter : h->launches_iter_cg;
     }
     AMG_CK(h, cudaMemcpyAsync(hs, h->st, sizeof(FcgState), cudaMemcpyDeviceToHost, s));
     AMG_CK(h, cudaStreamSynchronize(s));
+    if (hs->done || h->p.graph_batch <= 1) continue;
+    const int did = hs->it - it_prev;
+    double need = (double)h->p.graph_batch;
+    if (did > 0 && hs->res > 0.0 && hs->res < res_prev) {
+      const double rate = std::pow(hs->res / res_prev, 1.0 / did);  // per iteration, in (0, 1)
+      need = tol > 0.0 ? std::ceil(std::log(tol / hs->res) / std::log(rate)) : 64.0;
+    }
+    batch = (int)std::max(1.0, std::min({need, 64.0, (double)(maxit - hs->it)}));
+    res_prev = hs->res;
+    it_prev = hs->it;
   }
   if (hs->status != AMG_OK && hs->nb > 0.0) {
     launch_fcg_resid<RES_NORM>(h, s);
+    ++launches;
     AMG_CK(h, cudaMemcpyAsync(hs, h->st, sizeof(FcgState), cudaMemcpyDeviceToHost, s));
     AMG_CK(h, cudaStreamSynchronize(s));
   }
+  h->launches_last_solve = launches;
   amg_status fl = check_device_flags(h);
   if (fl != AMG_OK) return fl;
   if (iters) *iters = hs->it;
@@ -1519,13 +1592,13 @@ static amg_status launch_one(amg_handle* h, int which, int k) {
       Level& C = h->L[k + 1];
       bool ccoarse = (k + 1 == h->nl - 1);
       if (which == 2) {
-        if (!L.lowp) amg_launch(k_restrict<double, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (double*)L.t, (double*)C.r, skip, L.n);
-        else if (ccoarse) amg_launch(k_restrict<float, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (float*)L.t, (double*)C.r, skip, L.n);
-        else amg_launch(k_restrict<float, float>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (float*)L.t, (float*)C.r, skip, L.n);
+        if (!L.lowp) amg_launch(k_restrict<double, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (double*)L.t, (double*)C.r, skip, L.n, L.pwm);
+        else if (ccoarse) amg_launch(k_restrict<float, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (float*)L.t, (double*)C.r, skip, L.n, L.pwmf);
+        else amg_launch(k_restrict<float, float>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem, (float*)L.t, (float*)C.r, skip, L.n, L.pwmf);
       } else {
-        if (!L.lowp) amg_launch(k_prolong<double, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (double*)C.za, (double*)L.za, skip, C.n);
-        else if (ccoarse) amg_launch(k_prolong<float, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (double*)C.za, (float*)L.za, skip, C.n);
-        else amg_launch(k_prolong<float, float>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (float*)C.za, (float*)L.za, skip, C.n);
+        if (!L.lowp) amg_launch(k_prolong<double, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (double*)C.za, (double*)L.za, skip, C.n, L.pw);
+        else if (ccoarse) amg_launch(k_prolong<float, double>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (double*)C.za, (float*)L.za, skip, C.n, L.pwf);
+        else amg_launch(k_prolong<float, float>, dim3(ew_blocks(L.n)), dim3(AMG_BLOCK), 0, s, L.n, L.agg, (float*)C.za, (float*)L.za, skip, C.n, L.pwf);
       }
       break;
     }
@@ -1537,16 +1610,16 @@ static amg_status launch_one(amg_handle* h, int which, int k) {
       if (which == 6) {
         if (ccoarse && !L.lowp)
           amg_launch(k_restrict_first<double, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem,
-                     (const double*)L.t, (const double*)C.dinv, (double*)C.r, (double*)C.za, skip, L.n);
+                     (const double*)L.t, (const double*)C.dinv, (double*)C.r, (double*)C.za, skip, L.n, L.pwm);
         else if (ccoarse)
           amg_launch(k_restrict_first<float, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem,
-                     (const float*)L.t, (const double*)C.dinv, (double*)C.r, (double*)C.za, skip, L.n);
+                     (const float*)L.t, (const double*)C.dinv, (double*)C.r, (double*)C.za, skip, L.n, L.pwmf);
         else if (!L.lowp)
           amg_launch(k_restrict_first<double, double>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem,
-                     (const double*)L.t, (const double*)C.dinv, (double*)C.r, (double*)C.za, skip, L.n);
+                     (const double*)L.t, (const double*)C.dinv, (double*)C.r, (double*)C.za, skip, L.n, L.pwm);
         else
           amg_launch(k_restrict_first<float, float>, dim3(amg_blocks(C.n)), dim3(AMG_BLOCK), 0, s, C.n, L.mptr, L.mem,
-                     (const float*)L.t, (const float*)C.dinvf, (float*)C.r, (float*)C.za, skip, L.n);
+                     (const float*)L.t, (const float*)C.dinvf, (float*)C.r, (float*)C.za, skip, L.n, L.pwmf);
       } else {
         bool ok;
         if (ccoarse || !C.lowp)

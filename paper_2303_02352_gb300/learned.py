@@ -146,10 +146,27 @@ def _autograd():
         def backward(ctx, dy):
             return None, ctx.h.spmv(0, dy.contiguous())
 
-    return MLPFn, VCycleFn, SpMVFn
+    class LossFn(torch.autograd.Function):
+        """(1/m) ln(|r_m| / |r_0|), r_{t+1} = r_t - A B(omega) r_t, with its
+        gradient in every level's damping: both computed by the library
+        (amg_vcycle_loss); the function only hands them to autograd."""
+
+        @staticmethod
+        def forward(ctx, h, r0, m, *omegas):
+            for k, om in enumerate(omegas):
+                h.set_omega(k, om.detach())
+            loss, dom = h.vcycle_loss(r0.detach(), m, grad=True)
+            ctx.dom = dom
+            return torch.tensor(loss, dtype=torch.float64, device=r0.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            return (None, None, None, *[d * g for d in ctx.dom])
+
+    return MLPFn, VCycleFn, SpMVFn, LossFn
 
 
-MLPFn, VCycleFn, SpMVFn = _autograd()
+MLPFn, VCycleFn, SpMVFn, LossFn = _autograd()
 
 
 def level_features(h):
@@ -157,13 +174,9 @@ def level_features(h):
 
 
 def stationary_loss(h, omegas, r0, m: int):
-    """(1/m) ln(|r_m| / |r_0|) with r_{t+1} = r_t - A B(omega) r_t."""
-    import torch
-    r = r0
-    for _ in range(m):
-        z = VCycleFn.apply(h, r, *omegas)
-        r = r - SpMVFn.apply(h, z)
-    return (torch.log(torch.linalg.vector_norm(r)) - torch.log(torch.linalg.vector_norm(r0))) / m
+    """(1/m) ln(|r_m| / |r_0|) with r_{t+1} = r_t - A B(omega) r_t: the loss and
+    its gradient in the dampings come from the library (amg_vcycle_loss)."""
+    return LossFn.apply(h, r0, m, *omegas)
 
 
 def train(problems, steps: int = 200, m: int = 3, lr: float = 3e-3, seed: int = 0, net: Network | None = None,

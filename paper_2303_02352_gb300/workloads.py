@@ -286,6 +286,11 @@ def _config_entry(name: str):
     if m:
         N = int(m.group(1))
         return (lambda: poisson7(N)), N, f"7-pt Poisson {N}^3, b = A x*, x* ~ U(-1,1) seed {N}"
+    m = __import__("re").fullmatch(r"diffusion7_(\d+)", name)
+    if m:  # the 256^3 evaluation problem's recipe at another size
+        N = int(m.group(1))
+        return ((lambda: diffusion7(N, 2.0, 4000)), N,
+                f"7-pt log-normal diffusion {N}^3 (sigma 2, 8^3 blocks, seed 4000), b = A x*, x* seed {N}")
     raise KeyError(name)
 
 

@@ -181,3 +181,32 @@ def test_committed_network_gains_at_full_size(prec):
     assert res["learned_iters"] < res["plain_iters"], (res["learned_iters"], res["plain_iters"])
     assert res["use_learned"]
     res["handle"].close()
+
+
+def test_library_loss_equals_chain_of_vcycle_adjoints():
+    """amg_vcycle_loss (loss and adjoint of the m stationary steps in the library)
+    against the same loss composed here from one-V-cycle autograd Functions
+    (VCycleFn, SpMVFn) with torch arithmetic between them."""
+    from paper_2303_02352_gb300 import amg, learned as L
+    A = W.diffusion7(10, 2.0, 55)
+    g = H(A, coarse_size=40)
+    rng = np.random.default_rng(7)
+    oms = [torch.tensor(0.7 + 0.6 * rng.random(nk), device="cuda") for nk in g.info()["n"]]
+    r0 = torch.as_tensor(W.random_vector(A.n, 12), device="cuda")
+    m = 3
+    a = [o.clone().requires_grad_(True) for o in oms]
+    loss_lib = L.stationary_loss(g, a, r0, m)
+    loss_lib.backward()
+    b = [o.clone().requires_grad_(True) for o in oms]
+    r = r0
+    for _ in range(m):
+        r = r - L.SpMVFn.apply(g, L.VCycleFn.apply(g, r, *b))
+    loss_chain = (torch.log(torch.linalg.vector_norm(r)) - torch.log(torch.linalg.vector_norm(r0))) / m
+    loss_chain.backward()
+    assert abs(float(loss_lib) - float(loss_chain)) <= 1e-12 * abs(float(loss_chain))
+    for k in range(len(oms)):
+        assert rel(a[k].grad.cpu().numpy(), b[k].grad.cpu().numpy()) < 1e-10, k
+    # forms the adjoint does not cover are rejected
+    for kw in (dict(cycle=2), dict(prolong_scale=1)):
+        with pytest.raises(amg.AmgError):
+            H(A, coarse_size=40, **kw).vcycle_loss(r0, m)

@@ -4,10 +4,12 @@ Tolerances (FP64 path): aggregates and integer structure bit-exact; coarse
 operators equal to 1e-12 relative (bitwise expected: both sides sum in the
 same canonical order); l1 norms bitwise; one V-cycle to 1e-12 relative; FCG
 iteration counts within 1; solutions at the same iteration count to 1e-9
-relative.  Low-precision hierarchies: V-cycle to 1e-5 (FP32) / 2e-2 (BF16
-finest level) relative against the oracle's FP64 V-cycle and 1e-4 against the
-oracle's own emulation of the same precision; iterations within 2 of the
-emulation; true FP64 residual below the tolerance.
+relative, also element-wise (largest difference over the largest entry).
+Low-precision hierarchies: V-cycle to 1e-6 (FP32) / 1e-2 (BF16 finest level)
+relative against the oracle's FP64 V-cycle and 1e-6 (l2 and element-wise)
+against the oracle's own emulation of the same precision; iterations within 2
+of the emulation, the iterate at equal count to 1e-9 and the residual history
+to 2e-5 above 1e-8; true FP64 residual below the tolerance.
 """
 import numpy as np
 import pytest
@@ -38,6 +40,35 @@ def G(A, **kw):
 def rel(a, b):
     a, b = np.asarray(a), np.asarray(b)
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def maxerr(a, b):
+    """Largest element-wise difference, relative to the largest entry of b."""
+    a, b = np.asarray(a), np.asarray(b)
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+# Low-precision hierarchies (FP32 arithmetic inside the V-cycle) against the
+# oracle's emulation of the same cast points.  The two differ by the rounding
+# order of float sums, so the bars are a few times the largest gaps measured
+# on the GPU over every low-precision comparison of these tests (V-cycle 1.2e-7
+# relative l2 and 2.1e-7 element-wise; iterate at equal iteration count
+# 1.7e-10; residual history 4.7e-6 where it is above 1e-8, below which the
+# relative difference of two float-preconditioned runs grows as the residual
+# falls).  Against the FP64 oracle: FP32 hierarchy 1.0e-7, BF16 level-0 values
+# 3.5e-3.
+LOWP_VC = 1e-6
+LOWP_X_REL = 1e-9
+LOWP_HIST_REL = 2e-5
+LOWP_HIST_FLOOR = 1e-8
+LOWP_VS_FP64 = {1: 1e-6, 2: 1e-2}
+
+
+def hist_close(hg, ho):
+    """Residual histories of two low-precision runs agree where above the floor."""
+    hg, ho = np.asarray(hg), np.asarray(ho)
+    keep = ho > LOWP_HIST_FLOOR
+    return np.max(np.abs(hg[keep] - ho[keep]) / ho[keep]) < LOWP_HIST_REL
 
 
 PROBLEMS = {
@@ -79,6 +110,7 @@ def test_vcycle_and_spmv_parity(name):
         zg = g.vcycle(r).cpu().numpy()
         zo = o.vcycle(r)
         assert rel(zg, zo) < 1e-12
+        assert maxerr(zg, zo) < 1e-12
     x = W.random_vector(A.n, 7)
     for k in range(o.num_levels):
         xk = x[: o.level_n(k)]
@@ -99,6 +131,7 @@ def test_fcg_parity(name):
     xg = g.pcg_solve(b, tol=0.0, maxit=m)["x"].cpu().numpy()
     xo = o.fcg(b, tol=0.0, maxit=m)["x"]
     assert rel(xg, xo) < 1e-9
+    assert maxerr(xg, xo) < 1e-9
     # residual history
     hg = g.pcg_solve(b, tol=0.0, maxit=m)["hist"]
     assert np.allclose(hg, o.fcg(b, tol=0.0, maxit=m)["hist"], rtol=1e-8, atol=0)
@@ -241,12 +274,18 @@ def test_low_precision_hierarchy(name, prec):
     olo = O.Hierarchy(A, precision=prec)
     r = W.random_vector(A.n, 9)
     zg = g.vcycle(r).cpu().numpy()
-    assert rel(zg, olo.vcycle(r)) < 1e-4
-    assert rel(zg, o64.vcycle(r)) < (1e-5 if prec == 1 else 2e-2)
+    zlo = olo.vcycle(r)
+    assert rel(zg, zlo) < LOWP_VC and maxerr(zg, zlo) < LOWP_VC
+    assert rel(zg, o64.vcycle(r)) < LOWP_VS_FP64[prec]
     b = W.rhs_from_solution(A, W.random_vector(A.n, 1))
     rg, rlo = g.pcg_solve(b), olo.fcg(b)
     assert rg["status"] == 0 and rg["true_rel_res"] < 1e-6
     assert abs(rg["iters"] - rlo["iters"]) <= 2
+    m = min(rg["iters"], rlo["iters"])
+    xg = g.pcg_solve(b, tol=0.0, maxit=m)
+    xo = olo.fcg(b, tol=0.0, maxit=m)
+    assert rel(xg["x"].cpu().numpy(), xo["x"]) < LOWP_X_REL
+    assert hist_close(xg["hist"], xo["hist"])
 
 
 # ---------------------------------------------------------------------------
@@ -279,7 +318,8 @@ def test_full_size_hierarchy_bit_exact(big):
 def test_full_size_vcycle_and_solve(big):
     A, g, o = big
     r = W.random_vector(A.n, 11)
-    assert rel(g.vcycle(r).cpu().numpy(), o.vcycle(r)) < 1e-12
+    zg, zo = g.vcycle(r).cpu().numpy(), o.vcycle(r)
+    assert rel(zg, zo) < 1e-12 and maxerr(zg, zo) < 1e-12
     xs = W.random_vector(A.n, 2)
     b = W.rhs_from_solution(A, xs)
     res = g.pcg_solve(b)
@@ -289,7 +329,8 @@ def test_full_size_vcycle_and_solve(big):
     assert abs(np.linalg.norm(rr) / np.linalg.norm(b) - res["true_rel_res"]) < 1e-9
     # the oracle's first two FCG iterates
     xg = g.pcg_solve(b, tol=0.0, maxit=2)["x"].cpu().numpy()
-    assert rel(xg, o.fcg(b, tol=0.0, maxit=2)["x"]) < 1e-10
+    xo = o.fcg(b, tol=0.0, maxit=2)["x"]
+    assert rel(xg, xo) < 1e-10 and maxerr(xg, xo) < 1e-10
 
 
 @pytest.mark.parametrize("name", ["poisson16", "poisson32", "diff27_12"])
@@ -387,6 +428,32 @@ def test_long_row_kernel_forms(form, name, monkeypatch):
     assert G(A, precision=1).pcg_solve(b)["true_rel_res"] < 1e-6
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("name", ["diff27_12", "diff7_20", "poisson13"])
+def test_two_consumer_group_form(name, prec, monkeypatch):
+    """Levels with tiles of 32-128 rows in two consumer groups with half the
+    threads per row (AMG_NG=1) against the oracle: the row sums add in another
+    order than the standard form, so the bars are the oracle's."""
+    A = PROBLEMS[name]()
+    monkeypatch.setenv("AMG_NG", "1")
+    g = G(A, precision=prec)
+    info = g.info()
+    assert any(c == 2 for c in info["consumer_groups"]) == any(32 <= t <= 128 for t in info["tile_rows"])
+    o = O.Hierarchy(A, precision=prec)
+    r = W.random_vector(A.n, 8)
+    zg, zo = g.vcycle(r).cpu().numpy(), o.vcycle(r)
+    tol = 1e-12 if prec == 0 else LOWP_VC
+    assert rel(zg, zo) < tol and maxerr(zg, zo) < tol
+    assert rel(g.spmv(0, r).cpu().numpy(), o.spmv(0, r)) < 1e-14
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 9))
+    rg, ro = g.pcg_solve(b), o.fcg(b)
+    assert rg["status"] == 0 and rg["true_rel_res"] < 1e-6
+    assert abs(rg["iters"] - ro["iters"]) <= (1 if prec == 0 else 2)
+    m = min(rg["iters"], ro["iters"])
+    xg = g.pcg_solve(b, tol=0.0, maxit=m)["x"].cpu().numpy()
+    assert rel(xg, o.fcg(b, tol=0.0, maxit=m)["x"]) < (1e-9 if prec == 0 else LOWP_X_REL)
+
+
 def test_automatic_kernel_forms(big, monkeypatch):
     """The setup's automatic choices: standard stages everywhere by default
     (the 27-point FP64 fine level of 64^3 in 64-row tiles, 4 threads per row;
@@ -420,8 +487,9 @@ def test_jacobi_relaxation_parity(name, prec):
     A = PROBLEMS[name]()
     g, o = G(A, precision=prec, relax_type=0), O.Hierarchy(A, precision=prec, relax_type=0)
     r = W.random_vector(A.n, 14)
-    tol = 1e-12 if prec == 0 else 1e-4
-    assert rel(g.vcycle(r).cpu().numpy(), o.vcycle(r)) < tol
+    tol = 1e-12 if prec == 0 else LOWP_VC
+    zg, zo = g.vcycle(r).cpu().numpy(), o.vcycle(r)
+    assert rel(zg, zo) < tol and maxerr(zg, zo) < tol
     assert np.array_equal(g.l1(0), o.level_l1(0))
     b = W.rhs_from_solution(A, W.random_vector(A.n, 15))
     rg, ro = g.pcg_solve(b), o.fcg(b)
@@ -507,7 +575,9 @@ def test_wcycle_parity(prec):
     A = W.poisson7(20)
     g, o = G(A, cycle=2, precision=prec), O.Hierarchy(A, cycle=2, precision=prec)
     r = W.random_vector(A.n, 5)
-    assert rel(g.vcycle(r).cpu().numpy(), o.vcycle(r)) < (1e-12 if prec == 0 else 1e-4)
+    zg, zo = g.vcycle(r).cpu().numpy(), o.vcycle(r)
+    tol = 1e-12 if prec == 0 else LOWP_VC
+    assert rel(zg, zo) < tol and maxerr(zg, zo) < tol
     b = W.rhs_from_solution(A, W.random_vector(A.n, 6))
     rg, ro = g.pcg_solve(b), o.fcg(b)
     assert abs(rg["iters"] - ro["iters"]) <= (1 if prec == 0 else 2) and rg["true_rel_res"] < 1e-6
@@ -608,3 +678,138 @@ def test_full_size_27pt_vcycle_symmetry_and_solves(big27, prec):
     xs = W.exact_solution("diffusion27_128", A.n)
     err = np.linalg.norm(res["x"].cpu().numpy() - xs) / np.linalg.norm(xs)
     assert err < 1e-3
+
+
+# ---------------------------------------------------------------------------
+# periodic true-residual replacement of the low-precision hierarchies
+# (r <- b - A u every true_res_every iterations; the recurrences of Alg. 1 are
+# otherwise unchanged)
+
+@pytest.mark.parametrize("k", [1, 3])
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("name", ["poisson16", "diff7_20"])
+def test_true_residual_replacement_parity(name, prec, k):
+    A = PROBLEMS[name]()
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 1))
+    g = G(A, precision=prec, true_res_every=k)
+    o = O.Hierarchy(A, precision=prec, true_res_every=k)
+    rg, ro = g.pcg_solve(b), o.fcg(b)
+    assert rg["status"] == 0 and ro["status"] == 0 and rg["true_rel_res"] < 1e-6
+    assert abs(rg["iters"] - ro["iters"]) <= 2
+    nb = np.linalg.norm(b)
+    assert abs(rg["true_rel_res"] - np.linalg.norm(b - A.to_scipy() @ rg["x"].cpu().numpy()) / nb) < 1e-9
+    m = min(rg["iters"], ro["iters"])
+    xg = g.pcg_solve(b, tol=0.0, maxit=m)
+    xo = o.fcg(b, tol=0.0, maxit=m)
+    assert rel(xg["x"].cpu().numpy(), xo["x"]) < LOWP_X_REL
+    assert hist_close(xg["hist"], xo["hist"])
+
+
+@pytest.mark.parametrize("prec,k", [(1, 3), (2, 2), (2, 4)])
+def test_true_residual_replacement_signature(prec, k):
+    """Far past convergence (tol = 0) the recursive residual keeps falling while
+    b - A u stagnates at round-off: each replacement shows as a rise of the
+    history back to the true residual, exactly at the multiples of k."""
+    A = W.poisson7(14)
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 3))
+    M = 45
+    g = G(A, precision=prec, true_res_every=k)
+    res = g.pcg_solve(b, tol=0.0, maxit=M)
+    assert res["status"] == 1 and res["iters"] == M
+    hist = res["hist"]
+    plain = G(A, precision=prec, true_res_every=0).pcg_solve(b, tol=0.0, maxit=M)["hist"]
+    assert np.array_equal(hist[:k], plain[:k])
+    stag = int(np.argmax(plain < 1e-20))
+    assert 10 <= stag < M - 2 * k
+    S, nb = A.to_scipy(), np.linalg.norm(b)
+    tr = {it: np.linalg.norm(b - S @ g.pcg_solve(b, tol=0.0, maxit=it)["x"].cpu().numpy()) / nb
+          for it in range(1, M + 1)}
+    noise = np.median([tr[it] for it in range(stag, M + 1)])
+    assert noise < 1e-14
+    for it in range(stag, M + 1):
+        if it % k == 0:
+            assert 0.25 < hist[it] / tr[it] < 4.0, (it, hist[it], tr[it])
+            assert hist[it] > hist[it - 1], it
+        else:
+            assert hist[it] < hist[it - (it % k)], it
+    assert plain[M] < 1e-3 * noise
+    for it in range(k, stag - 4, k):
+        assert abs(hist[it] - tr[it]) <= 1e-8 * tr[it], (it, hist[it], tr[it])
+    # the oracle's emulation runs the same replacements (same history where it
+    # lies above the floor of the low-precision bar)
+    ho = O.Hierarchy(A, precision=prec, true_res_every=k).fcg(b, tol=0.0, maxit=M)["hist"]
+    assert hist_close(hist, ho)
+
+
+def test_fp64_hierarchy_never_replaces_the_residual():
+    A = W.diffusion7(12, 2.0, 5)
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 3))
+    ref = G(A).pcg_solve(b, tol=0.0, maxit=30)
+    for k in (1, 3):
+        r = G(A, true_res_every=k).pcg_solve(b, tol=0.0, maxit=30)
+        assert np.array_equal(r["hist"], ref["hist"])
+        assert np.array_equal(r["x"].cpu().numpy().view(np.uint64), ref["x"].cpu().numpy().view(np.uint64))
+
+
+# ---------------------------------------------------------------------------
+# setup and solve on a non-blocking side stream (the caller's torch stream)
+
+
+@pytest.mark.parametrize("np_", [1, 5])
+def test_setup_and_solve_on_side_stream(np_):
+    A = W.poisson7(40)
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 8))
+    ref = G(A, num_parts=np_)
+    o = O.Hierarchy(A, num_parts=np_)
+    rref = ref.pcg_solve(b)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        torch.cuda._sleep(20_000_000)  # the side stream is busy when the setup is issued
+        g = G(A, num_parts=np_)
+        rg = g.pcg_solve(b)
+    torch.cuda.synchronize()
+    assert g.num_levels == o.num_levels
+    for k in range(o.num_levels - 1):
+        assert np.array_equal(g.aggregates(k), o.level_agg(k))
+        assert np.array_equal(g.aggregates(k), ref.aggregates(k))
+    assert rg["iters"] == rref["iters"]
+    assert np.array_equal(rg["x"].cpu().numpy().view(np.uint64), rref["x"].cpu().numpy().view(np.uint64))
+
+
+# ---------------------------------------------------------------------------
+# full-size 27-point log-normal hierarchy (irregular aggregates, many matching
+# ties) against the oracle: aggregates of every level bit-exact, coarse
+# operators to 1e-12 (bitwise expected), one V-cycle to 1e-12
+
+
+@pytest.fixture(scope="module")
+def big27_oracle(big27):
+    A, _, _ = big27
+    return O.Hierarchy(A)
+
+
+def test_full_size_27pt_hierarchy_equals_oracle(big27, big27_oracle):
+    A, _, g = big27
+    o = big27_oracle
+    info = g.info()
+    assert info["num_levels"] == o.num_levels
+    assert info["n"] == [o.level_n(k) for k in range(o.num_levels)]
+    assert info["nnz"] == [o.level_nnz(k) for k in range(o.num_levels)]
+    for k in range(o.num_levels - 1):
+        assert np.array_equal(g.aggregates(k), o.level_agg(k)), k
+    for k in range(1, o.num_levels):
+        grp, gci, gv = g.level_csr(k)
+        orp, oci, ov = o.level_csr(k)
+        assert np.array_equal(grp, orp) and np.array_equal(gci, oci)
+        assert np.max(np.abs(gv - ov)) <= 1e-12 * np.max(np.abs(ov))
+        assert np.array_equal(gv.view(np.uint64), ov.view(np.uint64))
+    for k in range(o.num_levels):
+        assert np.array_equal(g.l1(k).view(np.uint64), o.level_l1(k).view(np.uint64))
+
+
+def test_full_size_27pt_vcycle_equals_oracle(big27, big27_oracle):
+    A, _, g = big27
+    r = W.random_vector(A.n, 11)
+    zg, zo = g.vcycle(r).cpu().numpy(), big27_oracle.vcycle(r)
+    assert rel(zg, zo) < 1e-12
+    assert maxerr(zg, zo) < 1e-12

@@ -49,6 +49,12 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+def maxerr(a, b):
+    """Largest element-wise difference, relative to the largest entry of b."""
+    a, b = np.asarray(a), np.asarray(b)
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
 @pytest.mark.parametrize("name", list(RAND))
 def test_hierarchy_bit_exact(name):
     A = RAND[name]()
@@ -73,7 +79,8 @@ def test_vcycle_spmv_and_fcg(name):
     g, o = G(A), O.Hierarchy(A)
     for seed in (1, 2):
         r = W.random_vector(A.n, seed)
-        assert rel(g.vcycle(r).cpu().numpy(), o.vcycle(r)) < 1e-12
+        zg, zo = g.vcycle(r).cpu().numpy(), o.vcycle(r)
+        assert rel(zg, zo) < 1e-12 and maxerr(zg, zo) < 1e-12
     x = W.random_vector(A.n, 7)
     for k in range(o.num_levels):
         xk = x[: o.level_n(k)]
@@ -84,7 +91,8 @@ def test_vcycle_spmv_and_fcg(name):
     assert abs(rg["iters"] - ro["iters"]) <= 1 and rg["true_rel_res"] < 1e-6
     m = min(rg["iters"], ro["iters"])
     xg = g.pcg_solve(b, tol=0.0, maxit=m)["x"].cpu().numpy()
-    assert rel(xg, o.fcg(b, tol=0.0, maxit=m)["x"]) < 1e-9
+    xo = o.fcg(b, tol=0.0, maxit=m)["x"]
+    assert rel(xg, xo) < 1e-9 and maxerr(xg, xo) < 1e-9
 
 
 # every kernel-form switch of the setup; each run is compared with the oracle
@@ -124,8 +132,10 @@ def test_low_precision(name, prec):
     g, olo, o64 = G(A, precision=prec), O.Hierarchy(A, precision=prec), O.Hierarchy(A)
     r = W.random_vector(A.n, 9)
     zg = g.vcycle(r).cpu().numpy()
-    assert rel(zg, olo.vcycle(r)) < 1e-4
-    assert rel(zg, o64.vcycle(r)) < (1e-5 if prec == 1 else 2e-2)
+    zlo = olo.vcycle(r)
+    # bars: a few times the gaps measured on the GPU (see test_gpu_parity.LOWP_*)
+    assert rel(zg, zlo) < 1e-6 and maxerr(zg, zlo) < 1e-6
+    assert rel(zg, o64.vcycle(r)) < (1e-6 if prec == 1 else 1e-2)
     b = W.rhs_from_solution(A, W.random_vector(A.n, 1))
     rg, rlo = g.pcg_solve(b), olo.fcg(b)
     assert rg["status"] == 0 and rg["true_rel_res"] < 1e-6

@@ -81,3 +81,31 @@ def test_noalloc_rejects_oversize_and_null(amg):
     assert b"exceeds" in lib.amg_last_error(None)
     st = lib.amg_residual_norm_noalloc(ctypes.byref(big), None, p, None, p, None)
     assert st == amg.ERR_INVALID_ARG
+
+
+def test_noalloc_at_the_size_that_fills_the_scratch_array(amg):
+    """n = 2,097,152 rows (7-point Poisson 128^3): 8,192 blocks, every partial
+    sum slot of the fixed array and the ticket counter right after them.  Two
+    calls in a row against scipy's b - A x."""
+    import scipy.sparse  # noqa: F401  (A.to_scipy)
+    A = W.poisson7(128)
+    assert A.n == 2_097_152
+    b_np = W.rhs_from_solution(A, W.random_vector(A.n, 41))
+    x_np = W.random_vector(A.n, 42)
+    ref = b_np - A.to_scipy() @ x_np
+    csr, keep = _csr(amg, A)
+    lib = amg.load()
+    b, x = torch.as_tensor(b_np).cuda(), torch.as_tensor(x_np).cuda()
+    stream = torch.cuda.current_stream()
+    for call in range(2):
+        r = torch.full((A.n,), float("nan"), dtype=torch.float64, device="cuda")
+        norms = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+        st = lib.amg_residual_norm_noalloc(ctypes.byref(csr), b.data_ptr(), x.data_ptr(), r.data_ptr(),
+                                           norms.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
+        assert st == amg.OK, lib.amg_last_error(None)
+        torch.cuda.synchronize()
+        rr = r.cpu().numpy()
+        assert np.max(np.abs(rr - ref)) <= 1e-14 * np.max(np.abs(b_np)), call
+        nr, nb = norms.cpu().numpy()
+        assert abs(nr - np.linalg.norm(ref)) <= 1e-12 * np.linalg.norm(ref), call
+        assert abs(nb - np.linalg.norm(b_np)) <= 1e-12 * np.linalg.norm(b_np), call
