@@ -146,7 +146,7 @@ struct amg_handle {
   int min_tpr = 1;             // tuning hook: least threads per row of the pipelined kernels
   int fuse = 1;                // restriction and prolongation fused into the coarse level's first / last sweep
   int use_big = 0;             // long-row form of the FP64 row kernels: 0 (off; measured best), 4 (4x stages, one thread per row), 2, 5
-  int use_ng = 0;              // 1: levels with tiles of 32-128 rows run two consumer groups with half the threads per row (sb = 6)
+  int use_ng = 2;              // levels with tiles of 32-128 rows in two consumer groups with half the threads per row (sb = 6): 0 none, 1 all kernels, 2 the FP64 outer kernels only (measured best)
   int use_pair = 0;            // consecutive row passes in one launch (0 never: measured slower; 1 on levels with room for the lag; 2 always)
   int pair_slack = -1;         // tiles of lag beyond the halo (-1: two rounds of the grid)
   int kb = AMG_MAXL;           // first level of the fused bottom (nl: none)

@@ -916,9 +916,10 @@ amg_status amg_finish_setup(amg_handle* h) {
       L.Rd = rbig;
       L.sbd = sbig;
     }
-    // two consumer groups with half the threads per row (tiles of 32-128 rows)
-    if (h->use_ng && L.pipe && L.sb == 1 && L.R >= 32 && L.R <= 128) L.sb = 6;
-    if (h->use_ng && L.piped && L.sbd == 1 && L.Rd >= 32 && L.Rd <= 128) L.sbd = 6;
+    // two consumer groups with half the threads per row (tiles of 32-128 rows):
+    // use_ng 1 on every kernel of the level, 2 on the FP64 outer kernels only
+    if (h->use_ng == 1 && L.pipe && L.sb == 1 && L.R >= 32 && L.R <= 128) L.sb = 6;
+    if (h->use_ng >= 1 && L.piped && L.sbd == 1 && L.Rd >= 32 && L.Rd <= 128) L.sbd = 6;
     AMG_ALLOC(h, L.l1, double, L.n);
     AMG_ALLOC(h, L.dinv, double, L.n);
     if (L.lowp) {
