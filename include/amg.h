@@ -275,6 +275,33 @@ amg_status amg_spgemm(int32_t m, int32_t k, int32_t n, const int32_t* a_row_ptr,
                       const double* a_val, const int32_t* b_row_ptr, const int32_t* b_col_idx, const double* b_val,
                       int32_t* c_row_ptr, int32_t* c_col_idx, double* c_val, int64_t* nnz_c, void* stream);
 
+/*
+ * Problem generators on the device (the paper's library generates the
+ * benchmark matrix on each process, Sec. 5 / App. A).  The N^3 grid's
+ * unknowns are numbered x + N y + N^2 z, Dirichlet unknowns eliminated.
+ * amg_stencil_size: *n = N^3 rows and *nnz entries of the points-point
+ *   stencil (points 7 or 27; N >= 3; nnz below 2^31, else AMG_ERR_INVALID_ARG).
+ * amg_generate_stencil: writes that CSR into caller-allocated device arrays
+ *   (row_ptr n+1, col_idx nnz, val nnz; columns ascending).  kblock NULL (7
+ *   points only): the integer Poisson stencil (6 on the diagonal, -1 off it).
+ *   Otherwise kblock (host, ceil(N/block)^3 float32, x fastest) gives the
+ *   coefficient of each block of block^3 cells; a link is
+ *   2 k_i k_j / (k_i + k_j) divided by |d|^2 off the axes, negated off the
+ *   diagonal, a link leaving the grid counts k_i, the diagonal sums the links
+ *   of its row in column order; every operation rounded on its own.  The call
+ *   synchronises stream (kblock is read during the call).
+ * amg_random_vector: out (device, n) = 2 U_i - 1, U_i the top 53 bits of
+ *   output i of SplitMix64 seeded with seed, times 2^-53.  Enqueued on stream.
+ * amg_csr_times: y = A x (device; A as amg_csr, square), each row's products
+ *   rounded and summed in column order from the first.  Enqueued on stream.
+ * Errors: AMG_ERR_INVALID_ARG, AMG_ERR_OOM, AMG_ERR_CUDA; amg_last_error(NULL).
+ */
+amg_status amg_stencil_size(int32_t N, int32_t points, int64_t* n, int64_t* nnz);
+amg_status amg_generate_stencil(int32_t N, int32_t points, const float* kblock, int32_t block, int32_t* row_ptr,
+                                int32_t* col_idx, double* val, void* stream);
+amg_status amg_random_vector(int64_t n, uint64_t seed, double* out, void* stream);
+amg_status amg_csr_times(const amg_csr* A, const double* x, double* y, void* stream);
+
 /* Self-check of the bounded device waits: launches one block that waits on a
  * barrier phase nothing completes, with a limit of limit_us microseconds
  * (1 .. 2,000,000).  Returns AMG_ERR_TIMEOUT when the wait gave up and

@@ -89,6 +89,10 @@ def load(path: str | None = None):
         "amg_residual_norm_noalloc": (I32, [ctypes.POINTER(amg_csr), P, P, P, P, P]),
         "amg_check_bounded_wait": (I32, [I32, P]),
         "amg_spgemm": (I32, [I32, I32, I32, P, P, P, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_int64), P]),
+        "amg_stencil_size": (I32, [I32, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+        "amg_generate_stencil": (I32, [I32, I32, P, I32, P, P, P, P]),
+        "amg_random_vector": (I32, [ctypes.c_int64, ctypes.c_uint64, P, P]),
+        "amg_csr_times": (I32, [ctypes.POINTER(amg_csr), P, P, P]),
         "amg_features": (I32, [P, I32, P]),
         "amg_set_omega": (I32, [P, I32, P]),
         "amg_mlp_workspace_bytes": (ctypes.c_size_t, [I32]),
@@ -153,9 +157,13 @@ class Hierarchy:
             v = A.values().to(device=dev, dtype=torch.float64).contiguous()
             n = A.shape[0]
         else:
-            rp = torch.as_tensor(np.asarray(A.row_ptr, dtype=np.int32)).to(dev)
-            ci = torch.as_tensor(np.asarray(A.col_idx, dtype=np.int32)).to(dev)
-            v = torch.as_tensor(np.asarray(A.val, dtype=np.float64)).to(dev)
+            def arr(x, dt_np, dt_t):  # host arrays or tensors on any device
+                if isinstance(x, torch.Tensor):
+                    return x.to(device=dev, dtype=dt_t).contiguous()
+                return torch.as_tensor(np.asarray(x, dtype=dt_np)).to(dev)
+            rp = arr(A.row_ptr, np.int32, torch.int32)
+            ci = arr(A.col_idx, np.int32, torch.int32)
+            v = arr(A.val, np.float64, torch.float64)
             n = int(A.n)
         self.n = n
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -396,6 +404,73 @@ def spgemm(a_row_ptr, a_col_idx, a_val, b_row_ptr, b_col_idx, b_val, ncols: int,
     if st != OK:
         raise AmgError(st, lib.amg_last_error(None).decode())
     return crp, cci[: nnz.value], cv[: nnz.value]
+
+
+def _call(st, lib):
+    if st != OK:
+        raise AmgError(st, lib.amg_last_error(None).decode())
+
+
+def generate_stencil(N: int, points: int = 7, kblock=None, block: int = 8, stream=None):
+    """amg_generate_stencil: the N^3 stencil matrix (points 7 or 27) in device
+    memory, as (row_ptr, col_idx, val) tensors.  kblock: the float32 values of
+    the ceil(N/block)^3 coefficient blocks (host array), or None for the
+    integer Poisson stencil (7 points)."""
+    import torch
+    lib = load()
+    n, nnz = ctypes.c_int64(0), ctypes.c_int64(0)
+    _call(lib.amg_stencil_size(int(N), int(points), ctypes.byref(n), ctypes.byref(nnz)), lib)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rp = torch.empty(n.value + 1, dtype=torch.int32, device=dev)
+    ci = torch.empty(nnz.value, dtype=torch.int32, device=dev)
+    v = torch.empty(nnz.value, dtype=torch.float64, device=dev)
+    kb = None if kblock is None else np.ascontiguousarray(kblock, dtype=np.float32)
+    s = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    _call(lib.amg_generate_stencil(int(N), int(points), None if kb is None else kb.ctypes.data, int(block),
+                                   _ptr(rp), _ptr(ci), _ptr(v), s), lib)
+    return rp, ci, v
+
+
+def random_vector(n: int, seed: int, stream=None):
+    """amg_random_vector: x_i = 2 U_i - 1 from the SplitMix64 stream ``seed`` (device)."""
+    import torch
+    lib = load()
+    out = torch.empty(int(n), dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))
+    s = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    _call(lib.amg_random_vector(int(n), int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out), s), lib)
+    return out
+
+
+def csr_times(rp, ci, v, x, stream=None):
+    """amg_csr_times: y = A x (device), each row summed in column order."""
+    import torch
+    lib = load()
+    y = torch.empty_like(x)
+    a = amg_csr(rp.numel() - 1, ci.numel(), _ptr(rp), _ptr(ci), _ptr(v))
+    s = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    _call(lib.amg_csr_times(ctypes.byref(a), _ptr(x), _ptr(y), s), lib)
+    return y
+
+
+def generate(name: str, stream=None):
+    """A named stencil workload built on the device: ((row_ptr, col_idx, val),
+    b, x*) with b = A x*, bit for bit the host generator's (workloads.config)."""
+    import torch
+    from . import workloads as W
+    r = W.recipe(name)
+    kb = None if r["sigma"] is None else W.block_values(r["N"], r["sigma"], r["seed"], r["block"])
+    rp, ci, v = generate_stencil(r["N"], r["points"], kb, r["block"], stream)
+    xs = random_vector(rp.numel() - 1, r["xseed"], stream)
+    b = csr_times(rp, ci, v, xs, stream)
+    torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    return (rp, ci, v), b, xs
+
+
+class DeviceCSR:
+    """A device CSR (int32 / float64 tensors) accepted by Hierarchy."""
+
+    def __init__(self, rp, ci, v):
+        self.n, self.row_ptr, self.col_idx, self.val = rp.numel() - 1, rp, ci, v
 
 
 # -- module-level calls (the Python form of amg_setup / amg_pcg_solve) ------

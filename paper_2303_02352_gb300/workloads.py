@@ -99,16 +99,20 @@ def _offsets(points: int):
     return sorted(offs, key=lambda d: (d[2], d[1], d[0]))
 
 
-def block_field(N: int, sigma: float, seed: int, block: int = 8) -> np.ndarray:
-    """Cellwise coefficient k = exp(sigma * g_B), g_B ~ N(0,1) per block^3 block.
-
-    The block values are rounded to float32 (and widened back): log, cos and exp
-    may differ in the last bit between math libraries, and the rounding makes
-    the matrix (and with it every tie of the matching) the same on every machine.
-    """
+def block_values(N: int, sigma: float, seed: int, block: int = 8) -> np.ndarray:
+    """k_B = exp(sigma * g_B), g_B ~ N(0,1), for the ceil(N/block)^3 blocks
+    (x fastest), rounded to float32: log, cos and exp may differ in the last
+    bit between math libraries, and the rounding makes the matrix (and with it
+    every tie of the matching) the same on every machine."""
     nb = -(-N // block)
     g = gaussian(seed, np.arange(nb ** 3, dtype=np.uint64))
-    kb = np.exp(sigma * g).astype(np.float32).astype(np.float64)
+    return np.exp(sigma * g).astype(np.float32)
+
+
+def block_field(N: int, sigma: float, seed: int, block: int = 8) -> np.ndarray:
+    """Cellwise coefficient: the value of the cell's block^3 block (block_values)."""
+    nb = -(-N // block)
+    kb = block_values(N, sigma, seed, block).astype(np.float64)
     c = np.arange(N) // block
     bz, by, bx = np.meshgrid(c, c, c, indexing="ij")
     return kb[(bx + nb * by + nb * nb * bz).ravel()]
@@ -253,9 +257,21 @@ def random_vector(n: int, seed: int) -> np.ndarray:
 
 
 def rhs_from_solution(A: CSR, xstar: np.ndarray) -> np.ndarray:
-    """b = A x* (input preparation for problems with a known solution)."""
+    """b = A x* (input preparation for problems with a known solution): each
+    row's products rounded, then added in column order from the first (the
+    order the device generator follows, so both give the same bits)."""
     prod = A.val * xstar[A.col_idx]
-    return np.add.reduceat(prod, A.row_ptr[:-1].astype(np.int64)) if A.n else np.zeros(0)
+    rp = np.asarray(A.row_ptr, dtype=np.int64)
+    lens = np.diff(rp)
+    b = np.zeros(A.n)
+    if A.n == 0:
+        return b
+    has = lens > 0
+    b[has] = prod[rp[:-1][has]]
+    for k in range(1, int(lens.max())):  # vectorised over the rows, sequential within a row
+        sel = lens > k
+        b[sel] = b[sel] + prod[rp[:-1][sel] + k]
+    return b
 
 
 def training_sigma(p: int) -> float:
@@ -291,6 +307,27 @@ def _config_entry(name: str):
         N = int(m.group(1))
         return ((lambda: diffusion7(N, 2.0, 4000)), N,
                 f"7-pt log-normal diffusion {N}^3 (sigma 2, 8^3 blocks, seed 4000), b = A x*, x* seed {N}")
+    raise KeyError(name)
+
+
+def recipe(name: str) -> dict:
+    """The stencil recipe of a named workload: grid N, points, coefficient
+    field (sigma, seed, block; sigma None for the constant Poisson stencil)
+    and the seed of x* -- what a generator on the device needs to build the
+    same matrix and right-hand side."""
+    m = __import__("re").fullmatch(r"poisson(\d+)", name)
+    if m:
+        N = int(m.group(1))
+        seeds = {"poisson32": 1, "poisson160": 2, "poisson320": 5}
+        return dict(N=N, points=7, sigma=None, seed=None, block=8, xseed=seeds.get(name, N))
+    fixed = {"diffusion27_128": dict(N=128, points=27, sigma=2.0, seed=3, block=8, xseed=3),
+             "diffusion7_256": dict(N=256, points=7, sigma=2.0, seed=4000, block=8, xseed=4)}
+    if name in fixed:
+        return dict(fixed[name])
+    m = __import__("re").fullmatch(r"diffusion7_(\d+)", name)
+    if m:
+        N = int(m.group(1))
+        return dict(N=N, points=7, sigma=2.0, seed=4000, block=8, xseed=N)
     raise KeyError(name)
 
 

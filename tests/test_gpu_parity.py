@@ -813,3 +813,21 @@ def test_full_size_27pt_vcycle_equals_oracle(big27, big27_oracle):
     zg, zo = g.vcycle(r).cpu().numpy(), big27_oracle.vcycle(r)
     assert rel(zg, zo) < 1e-12
     assert maxerr(zg, zo) < 1e-12
+
+
+@pytest.mark.parametrize("key", ["poisson32:fp64", "poisson160:fp64"])
+def test_against_stored_oracle_reference(key):
+    """The oracle's hierarchy and solve stored in tests/golden/oracle_reference.json
+    (written by a script that calls only the oracle): level sizes exact, the
+    operator complexity, iterations within 1, the true residual below 1e-6."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_reference.json")))[key]
+    name = key.split(":")[0]
+    A, b, _ = W.config(name)
+    g = G(A)
+    info = g.info()
+    assert info["num_levels"] == gold["levels"] and info["n"] == gold["n"] and info["nnz"] == gold["nnz"]
+    assert abs(info["opc"] - gold["opc"]) < 1e-12
+    res = g.pcg_solve(b)
+    assert res["status"] == 0 and abs(res["iters"] - gold["iters"]) <= 1 and res["true_rel_res"] < 1e-6
