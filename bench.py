@@ -186,10 +186,10 @@ def kernel_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload: str, precision: str, tile_rows: int, stage_scale: int):
+def ncu_traffic(workload: str, precision: str, tile_rows: int, stage_scale: int, column_patterns: int):
     """DRAM bytes per launch of the dominant kernel from the committed ncu record,
     or None when that record was taken on other kernel sources or another
-    launch shape (tile height, stage size) of the level-0 kernel."""
+    launch shape (tile height, stage size, column form) of the level-0 kernel."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -197,6 +197,8 @@ def ncu_traffic(workload: str, precision: str, tile_rows: int, stage_scale: int)
     if not d or d.get("kernel_digest") != kernel_digest():
         return None
     if d.get("tile_rows") != tile_rows or d.get("stage_scale") != stage_scale:
+        return None
+    if d.get("column_patterns", 0) != column_patterns:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -436,6 +438,20 @@ def main():
             gd.close()
         extras["setup_split_ms"] = {"total": info["setup_ms"], "matching": info["setup_match_ms"],
                                     "galerkin": info["setup_galerkin_ms"]}
+        # the same hierarchy with CSR column indices in every row kernel (no
+        # pattern-coded columns): same arithmetic, 4 bytes per entry more
+        os.environ["AMG_PAT"] = "0"
+        try:
+            gc = amg.Hierarchy(A, precision=PRECISIONS[args.precision])
+        finally:
+            del os.environ["AMG_PAT"]
+        ci = gc.info()
+        t_sw = gc.time_kernel(amg.K_SWEEP, 0, reps=30)
+        b_sw = gc.kernel_bytes(amg.K_SWEEP, 0)
+        extras["csr_columns"] = {**timed(gc), "vcycle_ms": gc.time_vcycle(reps=10), "vcycle_bytes": ci["vcycle_bytes"],
+                                 "sweep_ms": round(t_sw, 5), "sweep_bytes": b_sw,
+                                 "sweep_frac": round(b_sw / (t_sw * 1e-3) / 1e9 / peak, 4)}
+        gc.close()
         # w-normalised prolongator values (Sec. 3.1), level matrices by the general
         # sparse product: solve, and the setup split matching / pairwise Galerkin /
         # general product
@@ -457,11 +473,13 @@ def main():
                        "levels": info["num_levels"], "n": info["n"], "nnz": info["nnz"],
                        "opc": round(info["opc"], 4), "iters": iters,
                        "kernel_forms": {"tile_rows": info["tile_rows"], "stage_scale": info["stage_scale"],
-                                        "fused_bottom_from_level": info["bottom_level"]}},
+                                        "fused_bottom_from_level": info["bottom_level"],
+                                        "column_patterns": info["column_patterns"],
+                                        "outer_patterns": info["outer_patterns"]}},
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(ach / peak, 4),
                          "traffic": ncu_traffic(args.workload, args.precision, info["tile_rows"][0],
-                                                info["stage_scale"][0]),
+                                                info["stage_scale"][0], info["column_patterns"][0]),
                          "kernel": "l1-Jacobi sweep, level 0", "algorithmic_bytes_per_launch": by_sweep,
                          "launch_ms": round(t_sweep, 5), "peak_kind": peak_kind},
             "vcycle": {"ms": round(t_vc, 4), "bytes": info["vcycle_bytes"], "GB/s": round(vc_gbs, 1),

@@ -102,6 +102,14 @@ typedef struct {
   double setup_spgemm_ms;     /* setup time in the general sparse products (prolong_scale = 1) */
   int32_t last_solve_launches; /* kernel launches of the last solve on the handle (0 before any) */
   int32_t consumer_groups[40];  /* groups of consumer warps taking a level's tiles in turn (0: non-pipelined) */
+  int32_t column_patterns[40];  /* distinct column-offset tuples of a level whose V-cycle row kernels read
+                                   pattern-coded columns (a one-byte tuple id per row instead of a 4-byte
+                                   column index per entry; same entries and arithmetic); 0: CSR columns */
+  int32_t outer_patterns;       /* the same for the FP64 outer kernels on level 0 */
+  int32_t column_form[40];      /* 0 CSR columns; 1 pattern ids, rows located by row pointers; 2 pattern
+                                   ids, rows located from the tuple lengths and one row pointer per 32
+                                   rows (kernel forms with one thread per row) */
+  int32_t outer_column_form;    /* the same for the FP64 outer kernels on level 0 */
 } amg_info_t;
 
 typedef struct amg_handle amg_handle;

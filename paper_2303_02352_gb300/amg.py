@@ -54,7 +54,9 @@ class amg_info_t(ctypes.Structure):
                 ("setup_galerkin_ms", ctypes.c_double), ("bottom_level", ctypes.c_int32),
                 ("tile_rows", ctypes.c_int32 * 40), ("stage_scale", ctypes.c_int32 * 40),
                 ("setup_spgemm_ms", ctypes.c_double), ("last_solve_launches", ctypes.c_int32),
-                ("consumer_groups", ctypes.c_int32 * 40)]
+                ("consumer_groups", ctypes.c_int32 * 40), ("column_patterns", ctypes.c_int32 * 40),
+                ("outer_patterns", ctypes.c_int32), ("column_form", ctypes.c_int32 * 40),
+                ("outer_column_form", ctypes.c_int32)]
 
 
 _LIB = None
@@ -239,7 +241,9 @@ class Hierarchy:
                 "setup_match_ms": inf.setup_match_ms, "setup_galerkin_ms": inf.setup_galerkin_ms,
                 "bottom_level": inf.bottom_level, "tile_rows": list(inf.tile_rows[:L]),
                 "stage_scale": list(inf.stage_scale[:L]), "setup_spgemm_ms": inf.setup_spgemm_ms,
-                "last_solve_launches": inf.last_solve_launches, "consumer_groups": list(inf.consumer_groups[:L])}
+                "last_solve_launches": inf.last_solve_launches, "consumer_groups": list(inf.consumer_groups[:L]),
+                "column_patterns": list(inf.column_patterns[:L]), "outer_patterns": inf.outer_patterns,
+                "column_form": list(inf.column_form[:L]), "outer_column_form": inf.outer_column_form}
 
     @property
     def num_levels(self) -> int:

@@ -100,6 +100,21 @@ struct Level {
   double* pwm = nullptr;     // the same values in member order (restriction), n
   float* pwf = nullptr;      // float copies for a low-precision level
   float* pwmf = nullptr;
+  // pattern-coded columns (pattern.cu): the column indices of row i are
+  // i + ptab[pid[i] * pk + j] for its entries j = 0, 1, ...; rows with the same
+  // tuple of column offsets share one table row.  nullptr: CSR columns only.
+  uint8_t* pid = nullptr;
+  int32_t* ptab = nullptr;
+  int32_t* plen = nullptr;   // entries of each tuple
+  int32_t* pcb = nullptr;    // row_ptr at every 32nd row, and nnz: ceil(n / 32) + 1 entries
+  int npat = 0;              // table rows (distinct offset tuples), at most 255
+  int pk = 0;                // entries per table row (the longest row)
+  // column form of the pipelined V-cycle row kernels of this level: 0 CSR; 1
+  // pattern ids, rows located by row_ptr; 2 pattern ids, rows located from the
+  // tuple lengths (forms with one thread per row: a warp's 32 rows start at
+  // pcb and follow each other)
+  int pat = 0;
+  int patd = 0;              // the same for the FP64 outer kernels
   bool lowp = false;         // this level runs in float inside the V-cycle
   PairCtl* pctl = nullptr;   // paired-pass kernel state (pair.cuh): control word and per-tile counters
   unsigned* pcnt = nullptr;
@@ -147,6 +162,7 @@ struct amg_handle {
   int fuse = 1;                // restriction and prolongation fused into the coarse level's first / last sweep
   int use_big = 0;             // long-row form of the FP64 row kernels: 0 (off; measured best), 4 (4x stages, one thread per row), 2, 5
   int use_ng = 2;              // levels with tiles of 32-128 rows in two consumer groups with half the threads per row (sb = 6): 0 none, 1 all kernels, 2 the FP64 outer kernels only (measured best)
+  int use_pat = 1;             // pattern-coded columns on levels whose rows fall into at most 255 offset tuples: 0 never, 1 with row pointers (measured best), 2 with rows located from the tuple lengths where one thread takes a row
   int use_pair = 0;            // consecutive row passes in one launch (0 never: measured slower; 1 on levels with room for the lag; 2 always)
   int pair_slack = -1;         // tiles of lag beyond the halo (-1: two rounds of the grid)
   int kb = AMG_MAXL;           // first level of the fused bottom (nl: none)
@@ -198,6 +214,10 @@ static inline int amg_blocks(int64_t threads) { return (int)((threads + AMG_BLOC
 #ifndef PIPE_CONSUMERS
 #define PIPE_CONSUMERS 256
 #endif
+// largest offset table of a pattern-coded level (entries, pattern.cu): the
+// row kernels keep it in shared memory, and 4 KB per block keeps four FP64
+// blocks per multiprocessor
+#define PAT_TAB_MAX 1024
 #ifndef PIPE_STAGE_SCALE
 #define PIPE_STAGE_SCALE 1  // stages are 24/16/12 KB divided by this (FP64/FP32/BF16 values)
 #endif
@@ -223,6 +243,7 @@ amg_status amg_normalise_hierarchy(amg_handle* h);
 amg_status amg_build_members(amg_handle* h, int k);  // member lists of level k's aggregates (setup.cu)
 amg_status amg_member_values(amg_handle* h, int k);  // pwm of level k from pw and the member lists (spgemm.cu)
 amg_status amg_finish_setup(amg_handle* h);          // derived data, plan, work vectors, graphs (setup.cu)
+amg_status amg_build_patterns(amg_handle* h, int k); // pattern-coded columns of level k where they exist (pattern.cu)
 amg_status amg_check_level(amg_handle* h, int k, int nc);  // structure of a level read from a file (setup.cu)
 void amg_read_hooks(amg_handle* h);                  // test and tuning hooks from the environment (setup.cu)
 

@@ -56,7 +56,11 @@ extern "C" amg_status amg_info(const amg_handle* h, amg_info_t* info) {
     info->tile_rows[k] = L.pipe ? L.R : 0;
     info->stage_scale[k] = L.pipe ? (L.sb == 5 ? 2 : (L.sb == 6 ? 1 : L.sb)) : 0;
     info->consumer_groups[k] = L.pipe ? ((L.sb == 5 || L.sb == 6) ? 2 : 1) : 0;
+    info->column_patterns[k] = L.pat ? L.npat : 0;
+    info->column_form[k] = L.pat;
   }
+  info->outer_patterns = h->nl > 0 && h->L[0].patd ? h->L[0].npat : 0;
+  info->outer_column_form = h->nl > 0 ? h->L[0].patd : 0;
   return AMG_OK;
 }
 

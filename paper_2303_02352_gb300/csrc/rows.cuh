@@ -25,17 +25,20 @@
 // kernels need)
 // SB scales the stage: SB = 4 (FP64 only) holds 256 rows of up to 32 entries,
 // so long-row levels keep one thread per row (see launch_rows)
-template <typename MT, int SB = 1>
+// SMALL (pattern-coded columns): the same value capacity, and room for the
+// tile's one-byte row ids instead of its column indices; the smaller stage
+// lets more blocks share a multiprocessor (FP64: six instead of four)
+template <typename MT, int SB = 1, bool PAT = false>
 struct PipeTile {
   static constexpr int VE = 16 / (int)sizeof(MT);
   static constexpr int CAP = amg_pipe_tile_bytes((int)sizeof(MT)) * SB / ((int)sizeof(MT) + 4);
   MT v[CAP + 2 * VE];
-  int32_t c[CAP + 8];
+  int32_t c[PAT ? (PIPE_CONSUMERS + 16) / 4 : CAP + 8];
 };
 
-template <typename MT, int S, int SB = 1>
+template <typename MT, int S, int SB = 1, bool PAT = false>
 struct PipeSmem {
-  PipeTile<MT, SB> st[S];
+  PipeTile<MT, SB, PAT> st[S];
   unsigned long long full[S];   // producer -> consumers: the stage holds the tile
   unsigned long long empty[S];  // consumers -> producer: every consumer warp has read it
 };
@@ -98,6 +101,20 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
 enum { PM_SWEEP = 0, PM_RESID = 1, PM_SPMV = 2, PM_DOTS = 3, PM_RINIT = 4, PM_RTRUE = 5, PM_RNORM = 6,
        PM_SWEEP_PROLONG = 7 };
 
+// stage of a pattern-coded kernel: the small one (values and ids), except for
+// the outer SpMV with dot products, which measured faster in four blocks of
+// full stages per multiprocessor than in six of small ones (7-point Poisson
+// 320^3: 615 vs 665 us).  The V-cycle kernels all take the small stage: taken
+// alone the FP64 sweep is faster in full stages (553 vs 572 us) and the
+// residual in small ones (446 vs 532 us), but a V-cycle that alternates the
+// two footprints ran 6% slower than either uniform choice (5.83 vs 5.47-5.49
+// ms): consecutive launches overlap (programmatic dependent launch) only where
+// a finished block's slot fits a block of the next kernel.
+template <typename MT, int MODE, int PAT>
+__host__ __device__ constexpr bool pat_small() {
+  return PAT > 0 && MODE != PM_DOTS;
+}
+
 template <typename MT, typename VT, typename OT>
 struct RowArgs {
   int n;
@@ -121,7 +138,16 @@ struct RowArgs {
   void* zf;
   int zf64;  // the finer iterate is double (else float)
   int nf;    // rows of the finer level (bounds-checked builds)
+  // pattern-coded columns (PAT forms): row i's columns are i + ptab[pid[i] * pk + j]
+  const uint8_t* pid;
+  const int32_t* ptab;
+  int pk;
+  int ptab_n;           // table entries
+  const int32_t* plen;  // entries of each tuple (npat)
+  int npat;
+  const int32_t* pcb;   // PAT = 2: row_ptr at every 32nd row, and nnz
 };
+
 
 // z_f[i] += z for the members i of aggregate `row`, in the finer level's
 // vector type.  The TPR lanes of the row share the members (lane `sub` takes
@@ -178,14 +204,30 @@ __device__ __forceinline__ bool mbar_wait_warp(unsigned long long* bar, uint32_t
 // in turn (group g: tiles g, g + NG, ...): tiles of R = PIPE_CONSUMERS / NG /
 // TPR rows, S stages in flight, each stage read by one group.  Long rows then
 // keep one thread per row with more, smaller stages in flight.
-template <int TPR, int S, int MODE, typename MT, typename VT, typename OT, int SB = 1, int NG = 1>
+//
+// PAT > 0: the level's columns are pattern-coded (pattern.cu).  The second
+// copy of a tile moves its rows' one-byte pattern ids instead of the entries'
+// column indices, and entry j of row i gathers x[i + ptab[id * pk + j]]; the
+// table and the tuple lengths (at most 4 KB) are copied into shared memory
+// behind the stages when the block starts, so an offset costs what a staged
+// column index cost (read through L1 instead, the offset load added a
+// dependent round trip before every gather: 7-point FP64 sweep 0.610 -> 0.647
+// ms at 320^3, measured).  PAT = 2 (one thread per row) also leaves row_ptr
+// unread: a warp's 32 rows are consecutive, start at pcb[first row / 32], and
+// each row starts where the previous one ends (a warp scan of the tuple
+// lengths).  Same entries, same order, same arithmetic in every form.
+template <int TPR, int S, int MODE, typename MT, typename VT, typename OT, int SB = 1, int NG = 1, int PAT = 0>
 __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs<MT, VT, OT> a) {
   static_assert(S % NG == 0, "each stage is read by one group");
+  static_assert(PAT != 2 || TPR == 1, "rows located from the tuple lengths: one thread per row");
+  constexpr bool CB = PAT == 2;
   constexpr int CG = PIPE_CONSUMERS / NG;  // consumer threads per group
   constexpr int R = CG / TPR;
   pdl_trigger();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  auto* P = reinterpret_cast<PipeSmem<MT, S, SB>*>(smem_raw);
+  constexpr bool SMALL = pat_small<MT, MODE, PAT>();
+  auto* P = reinterpret_cast<PipeSmem<MT, S, SB, SMALL>*>(smem_raw);
+  int32_t* tab = reinterpret_cast<int32_t*>(smem_raw + sizeof(PipeSmem<MT, S, SB, SMALL>));  // PAT: offsets, lengths
   __shared__ double red[96];
   constexpr int VE = PipeTile<MT>::VE;
   constexpr int NCW = PIPE_CONSUMERS / 32;  // consumer warps
@@ -201,6 +243,10 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
     }
     mbar_fence_init();
   }
+  if constexpr (PAT > 0) {  // setup data: valid before the previous kernel ends
+    for (int j = threadIdx.x; j < a.ptab_n; j += blockDim.x) tab[j] = __ldg(&a.ptab[j]);
+    for (int j = threadIdx.x; j < a.npat; j += blockDim.x) tab[a.ptab_n + j] = __ldg(&a.plen[j]);
+  }
   __syncthreads();
 
   // copies of this block's k-th tile (producer lane only); the matrix does not
@@ -209,13 +255,18 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
   auto issue = [&](int k, int stage) {
     const int tile = blockIdx.x + k * G;
     const int row0 = tile * R, row1 = min(row0 + R, n);
-    const int p0 = __ldg(&a.rp[row0]), p1 = __ldg(&a.rp[row1]);
+    // row0 is a multiple of 32 and row1 one or n
+    const int p0 = CB ? __ldg(&a.pcb[row0 >> 5]) : __ldg(&a.rp[row0]);
+    const int p1 = CB ? __ldg(&a.pcb[(row1 + 31) >> 5]) : __ldg(&a.rp[row1]);
     const int av = p0 & ~(VE - 1), ac = p0 & ~3;
     const uint32_t bv = (uint32_t)(((p1 - av) * (int)sizeof(MT) + 15) & ~15);
-    const uint32_t bc = (uint32_t)(((p1 - ac) * 4 + 15) & ~15);
+    // PAT: the ids of rows row0 .. row1-1 (row0 is a multiple of R >= 32, so
+    // the source is 16-byte aligned; the allocation is padded past n)
+    const uint32_t bc = PAT > 0 ? (uint32_t)((row1 - row0 + 15) & ~15) : (uint32_t)(((p1 - ac) * 4 + 15) & ~15);
     mbar_expect_tx(&P->full[stage], bv + bc);
     tma_load_1d(P->st[stage].v, a.v + av, bv, &P->full[stage]);
-    tma_load_1d(P->st[stage].c, a.ci + ac, bc, &P->full[stage]);
+    if constexpr (PAT > 0) tma_load_1d(P->st[stage].c, a.pid + row0, bc, &P->full[stage]);
+    else tma_load_1d(P->st[stage].c, a.ci + ac, bc, &P->full[stage]);
   };
   const bool producer = warp == NCW && lane == 0;
   int issued = 0;
@@ -277,12 +328,16 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
       const int row = row0 + tg / TPR;
       const bool live = row < row1;
       const bool lead = live && sub == 0;      // the lane that finishes the row
-      const int p0 = __ldg(&a.rp[row0]);
-      int q0 = 0, q1 = 0;
+      const int p0 = CB ? __ldg(&a.pcb[row0 >> 5]) : __ldg(&a.rp[row0]);
+      int q0 = 0, q1 = 0, qs = 0;
       VT own = 0, rr = 0, dd = 0, qq = 0;
       OT zn = 0;  // PM_SWEEP_PROLONG: the row's new value
-      if (live) {
-        q0 = __ldg(&a.rp[row]) + sub;
+      int wbase = 0;  // CB: first entry of the warp's first row
+      if constexpr (CB) {
+        if (row - lane < n) wbase = __ldg(&a.pcb[(row - lane) >> 5]);
+      } else if (live) {
+        qs = __ldg(&a.rp[row]);
+        q0 = qs + sub;
         q1 = __ldg(&a.rp[row + 1]);
       }
       if (lead) {
@@ -305,7 +360,7 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
         break;
       }
       const int av = p0 & ~(VE - 1), ac = p0 & ~3;
-      const PipeTile<MT, SB>& T = P->st[stage];
+      const PipeTile<MT, SB, SMALL>& T = P->st[stage];
       // residuals, and sweeps in standard stages, accumulate
       // r_i - sum_j a_ij x_j from r_i (the lead lane holds r_i, the others 0):
       // one FP64 operation per row fewer than summing first and subtracting, on
@@ -317,7 +372,33 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
       constexpr bool FROM_R =
           MODE == PM_RESID || ((MODE == PM_SWEEP || MODE == PM_SWEEP_PROLONG) && SB == 1 && NG == 1);
       VT s = 0;
-      if constexpr (FROM_R) {
+      if constexpr (PAT > 0) {
+        // the row's offsets, indexed by entry position within the row
+        const int pr = live ? (int)reinterpret_cast<const uint8_t*>(T.c)[row - row0] : 0;
+        const int32_t* po = tab + pr * a.pk;
+        if constexpr (CB) {  // the row's entries: after those of the warp's earlier rows
+          const int len = live ? tab[a.ptab_n + pr] : 0;
+          int incl = len;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+          }
+          qs = wbase + incl - len;
+          q0 = qs;
+          q1 = qs + len;
+        }
+        if constexpr (FROM_R) {
+          s = rr;
+#pragma unroll 8
+          for (int q = q0; q < q1; q += TPR)
+            s -= (VT)to_acc(T.v[q - av]) * __ldg(&a.x[amg_chk(row + po[q - qs], n)]);
+        } else {
+#pragma unroll 8
+          for (int q = q0; q < q1; q += TPR)
+            s += (VT)to_acc(T.v[q - av]) * __ldg(&a.x[amg_chk(row + po[q - qs], n)]);
+        }
+      } else if constexpr (FROM_R) {
         s = rr;
 #pragma unroll 8
         for (int q = q0; q < q1; q += TPR) s -= (VT)to_acc(T.v[q - av]) * __ldg(&a.x[amg_chk(T.c[q - ac], n)]);
@@ -385,19 +466,34 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
   }
 }
 
+// dynamic shared memory of a pipelined row kernel: the stages and barriers,
+// and for the pattern forms the offset table (16-byte granules)
+template <typename MT, int S, int SB, int MODE, int PAT>
+static constexpr int pipe_smem(int tab_n) {
+  return (int)sizeof(PipeSmem<MT, S, SB, pat_small<MT, MODE, PAT>()>) + (PAT > 0 ? ((tab_n * 4 + 15) & ~15) : 0);
+}
+
 // grid of a persistent pipelined kernel: one wave of resident blocks, at most
 // one block per tile
-template <int TPR, int S, int MODE, typename MT, typename VT, typename OT, int SB = 1, int NG = 1>
-static int pipe_grid(int n) {
-  static int bps = -1;
-  constexpr int smem = (int)sizeof(PipeSmem<MT, S, SB>);
+
+template <int TPR, int S, int MODE, typename MT, typename VT, typename OT, int SB = 1, int NG = 1, int PAT = 0>
+static int pipe_grid(int n, int tab_n = 0) {
+  // resident blocks per multiprocessor, by table size in 256-byte steps
+  static int bps_by[PAT_TAB_MAX * 4 / 256 + 1] = {0};
+  static bool attr = false;
   constexpr int R = PIPE_CONSUMERS / NG / TPR;
-  auto kern = k_rows_pipe<TPR, S, MODE, MT, VT, OT, SB, NG>;
-  if (bps < 0) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  auto kern = k_rows_pipe<TPR, S, MODE, MT, VT, OT, SB, NG, PAT>;
+  if (!attr) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pipe_smem<MT, S, SB, MODE, PAT>(PAT_TAB_MAX));
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    attr = true;
+  }
+  int& bps = bps_by[PAT > 0 ? (tab_n * 4 + 255) / 256 : 0];
+  if (bps <= 0) {  // sized for the table rounded up to its 256-byte step
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, PIPE_CONSUMERS + 32, smem);
+    const size_t occ = sizeof(PipeSmem<MT, S, SB, pat_small<MT, MODE, PAT>()>) +
+                       (PAT > 0 ? (size_t)((tab_n * 4 + 255) & ~255) : 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, PIPE_CONSUMERS + 32, occ);
     bps = b < 1 ? 1 : b;
   }
   const int ntiles = (n + R - 1) / R;
@@ -405,9 +501,11 @@ static int pipe_grid(int n) {
   return ntiles < g ? ntiles : g;
 }
 
-template <int TPR, int S, int MODE, typename MT, typename VT, typename OT, int SB = 1, int NG = 1>
+template <int TPR, int S, int MODE, typename MT, typename VT, typename OT, int SB = 1, int NG = 1, int PAT = 0>
 static void launch_pipe(cudaStream_t s, const RowArgs<MT, VT, OT>& a) {
-  const int grid = pipe_grid<TPR, S, MODE, MT, VT, OT, SB, NG>(a.n);
-  constexpr int smem = (int)sizeof(PipeSmem<MT, S, SB>);
-  amg_launch(k_rows_pipe<TPR, S, MODE, MT, VT, OT, SB, NG>, dim3(grid), dim3(PIPE_CONSUMERS + 32), (size_t)smem, s, a);
+  const int tab_n = PAT > 0 ? a.ptab_n + a.npat : 0;  // offsets, then lengths
+  const int grid = pipe_grid<TPR, S, MODE, MT, VT, OT, SB, NG, PAT>(a.n, tab_n);
+  const int smem = pipe_smem<MT, S, SB, MODE, PAT>(tab_n);
+  amg_launch(k_rows_pipe<TPR, S, MODE, MT, VT, OT, SB, NG, PAT>, dim3(grid), dim3(PIPE_CONSUMERS + 32), (size_t)smem, s,
+             a);
 }

@@ -920,6 +920,18 @@ amg_status amg_finish_setup(amg_handle* h) {
     // use_ng 1 on every kernel of the level, 2 on the FP64 outer kernels only
     if (h->use_ng == 1 && L.pipe && L.sb == 1 && L.R >= 32 && L.R <= 128) L.sb = 6;
     if (h->use_ng >= 1 && L.piped && L.sbd == 1 && L.Rd >= 32 && L.Rd <= 128) L.sbd = 6;
+    // pattern-coded columns (pattern.cu), read by the pipelined forms that have
+    // a pattern variant: standard stages with tiles of 64-256 rows, two groups
+    if (L.pipe || L.piped) {
+      amg_status sp = amg_build_patterns(h, k);
+      if (sp != AMG_OK) return sp;
+    }
+    auto pat_form = [&](int R, int sb) {  // 2: one thread per row; 1: the other pattern forms
+      if ((sb == 1 && R == 256) || (sb == 6 && R == 128)) return h->use_pat >= 2 ? 2 : 1;
+      return ((sb == 1 && R >= 64) || sb == 6) ? 1 : 0;
+    };
+    L.pat = L.pid && L.pipe ? pat_form(L.R, L.sb) : 0;
+    L.patd = L.pid && L.piped ? pat_form(L.Rd, L.sbd) : 0;
     AMG_ALLOC(h, L.l1, double, L.n);
     AMG_ALLOC(h, L.dinv, double, L.n);
     if (L.lowp) {
@@ -965,6 +977,9 @@ void amg_read_hooks(amg_handle* h) {
   // AMG_PAIR=0/1/2 paired row passes never / where they pay / always,
   // AMG_PAIR_SLACK lag of the paired passes beyond the halo (tiles),
   // AMG_SMALL_ROWS, AMG_MIN_TPR row-kernel forms,
+  // AMG_PAT=0/1 CSR columns on every level / pattern-coded columns located
+  // by row pointers only (AMG_PAT=2: rows located from the tuple lengths
+  // where one thread takes a row),
   // AMG_SUITOR_CAP step cap of the matching loop,
   // AMG_FAIL_ALLOC_AFTER make the k-th device allocation of the handle fail
   if (const char* e = getenv("AMG_SUITOR_CAP")) h->suitor_cap = atoll(e);
@@ -978,6 +993,7 @@ void amg_read_hooks(amg_handle* h) {
   if (const char* e = getenv("AMG_FAIL_ALLOC_AFTER")) h->fail_alloc_after = atoi(e);
   if (const char* e = getenv("AMG_PIPE")) h->use_pipe = atoi(e);
   if (const char* e = getenv("AMG_NG")) h->use_ng = atoi(e);
+  if (const char* e = getenv("AMG_PAT")) h->use_pat = atoi(e);
 }
 
 extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* stream, amg_handle** out) {

@@ -540,11 +540,49 @@ int amg_num_sms() {
     default: { constexpr int TP = 4; CALL; } break;            \
   }
 
+// pattern-coded forms: standard stages with 1, 2 or 4 threads per row (tiles
+// of 256, 128, 64 rows) and the two-group form; the setup enables the pattern
+// form of a level only for these (pat_form in setup.cu)
+#define DISPATCH_TPR_PAT(TT, CALL)                      \
+  switch (TT) {                                         \
+    case 1: { constexpr int TP = 1; CALL; } break;      \
+    case 2: { constexpr int TP = 2; CALL; } break;      \
+    default: { constexpr int TP = 4; CALL; } break;     \
+  }
+
+// the pattern-coded columns of level L in a row kernel's arguments (form: the
+// column form of this launch's kernel, Level::pat / patd); pcb set selects the
+// form that locates rows from the tuple lengths
+template <typename MT, typename VT, typename OT>
+static inline void use_patterns(RowArgs<MT, VT, OT>& a, const Level& L, int form) {
+  if (!form || !L.pid) return;
+  a.pid = L.pid;
+  a.ptab = L.ptab;
+  a.pk = L.pk;
+  a.ptab_n = L.npat * L.pk;
+  a.plen = L.plen;
+  a.npat = L.npat;
+  a.pcb = form == 2 ? L.pcb : nullptr;
+}
+
 // sb = 2 / 4: FP64 level with long rows in 2x / 4x stages (R = 128 with two
 // threads per row / R = 256 with one); sb = 5: two consumer groups taking
 // tiles in turn, R = 128 rows with one thread per row, four 2x stages
 template <int MODE, typename MT, typename VT, typename OT>
 static void launch_rows(cudaStream_t s, int R, int sb, const RowArgs<MT, VT, OT>& a) {
+  if constexpr (MODE != PM_SWEEP_PROLONG) {  // latency-bound levels only: no pattern form
+    if (a.pid) {
+      if (a.pcb) {  // one thread per row: R = 128 in two groups, or R = 256
+        if (sb == 6) launch_pipe<1, 4, MODE, MT, VT, OT, 1, 2, 2>(s, a);
+        else launch_pipe<1, 2, MODE, MT, VT, OT, 1, 1, 2>(s, a);
+      } else if (sb == 6) {
+        DISPATCH_NG(R, (launch_pipe<TP, 4, MODE, MT, VT, OT, 1, 2, 1>(s, a)));
+      } else {
+        DISPATCH_TPR_PAT(PIPE_CONSUMERS / R, (launch_pipe<TP, 2, MODE, MT, VT, OT, 1, 1, 1>(s, a)));
+      }
+      return;
+    }
+  }
   if (sb == 6) {
     DISPATCH_NG(R, (launch_pipe<TP, 4, MODE, MT, VT, OT, 1, 2>(s, a)));
     return;
@@ -572,6 +610,7 @@ static void launch_sweep(cudaStream_t s, const Level& L, const MT* vals, const V
   const int R = L.R;
   if (L.pipe) {
     RowArgs<MT, VT, OT> a{L.n, L.rp, L.ci, vals, z, dinv, r, nullptr, nullptr, out, skip, nullptr, nullptr, nullptr, flags};
+    use_patterns(a, L, L.pat);
     launch_rows<PM_SWEEP>(s, R, L.sb, a);
     return;
   }
@@ -620,6 +659,7 @@ static void launch_resid(cudaStream_t s, const Level& L, const MT* vals, const V
   const int R = L.R;
   if (L.pipe) {
     RowArgs<MT, VT, VT> a{L.n, L.rp, L.ci, vals, z, nullptr, r, nullptr, nullptr, t, skip, nullptr, nullptr, nullptr, flags};
+    use_patterns(a, L, L.pat);
     launch_rows<PM_RESID>(s, R, L.sb, a);
     return;
   }
@@ -666,6 +706,7 @@ static void launch_dots(amg_handle* h, cudaStream_t s) {
   if (L.piped) {
     RowArgs<double, double, double> a{L.n, L.rp, L.ci, L.v, h->w, nullptr, h->r, nullptr, h->q, h->v,
                                       nullptr, h->st, h->partial, h->counter, h->dev_flags};
+    use_patterns(a, L, L.patd);
     launch_rows<PM_DOTS>(s, L.Rd, L.sbd, a);
     return;
   }
@@ -682,6 +723,7 @@ static void launch_fcg_resid(amg_handle* h, cudaStream_t s) {
     RowArgs<double, double, double> a{L.n, L.rp, L.ci, L.v, h->u, nullptr, nullptr, h->b, nullptr,
                                       MODE == RES_NORM ? nullptr : h->r, nullptr, h->st, h->partial, h->counter,
                                       h->dev_flags};
+    use_patterns(a, L, L.patd);
     launch_rows<PM>(s, L.Rd, L.sbd, a);
     return;
   }
@@ -708,7 +750,14 @@ struct VRec {
 
 // algorithmic bytes: a row pass reads the row pointers, every value and column
 // index once, and (by cache reuse) the gathered vector once
-static double row_pass(const Level& L, double sv) { return (double)L.nnz * (sv + 4.0) + 4.0 * (L.n + 1.0); }
+// index once; with pattern-coded columns (form 1) one id byte per row replaces
+// the column indices (the table of offsets is a few KB), and form 2 reads one
+// row pointer per 32 rows instead of one per row
+static double row_pass(const Level& L, double sv, int form = 0) {
+  if (!form || !L.pid) return (double)L.nnz * (sv + 4.0) + 4.0 * (L.n + 1.0);
+  const double ptrs = form == 2 ? 4.0 * ((L.n + 31) / 32 + 1.0) : 4.0 * (L.n + 1.0);
+  return (double)L.nnz * sv + ptrs + (double)L.n;
+}
 static double val_bytes(const Level& L) { return L.lowp ? (L.vb ? 2.0 : 4.0) : 8.0; }
 static double vec_bytes(const Level& L) { return L.lowp ? 4.0 : 8.0; }
 
@@ -759,7 +808,7 @@ static double* rec_coarse(VRec& R, int k, const double* r, double* final_out, bo
       R.add(row_pass(L, 8.0) + 32.0 * n + prolong_fused_bytes(*pro->F, L));
     } else {
       launch_sweep<double, double, double>(R.s, L, L.v, L.dinv, r, cur, nxt, R.skip, R.h->dev_flags);
-      R.add(row_pass(L, 8.0) + 32.0 * n);
+      R.add(row_pass(L, 8.0, L.pat) + 32.0 * n);
     }
     cur = nxt;
   }
@@ -1008,7 +1057,7 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
       double* zc2 = rec_coarse(R, k + 1, r2, nullptr);
       amg_launch(k_add<double>, dim3(ew_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, zc2, e, R.skip);
       R.add(16.0 * nc);
-      R.add(row_pass(C, 8.0) + 24.0 * nc);
+      R.add(row_pass(C, 8.0, C.pat) + 24.0 * nc);
       R.add(24.0 * nc);
       zc = e;
     }
@@ -1045,7 +1094,7 @@ static void rec_child(VRec& R, int k, const VT* t, VT* z) {
       else zc2 = (VT*)rec_level<double, double, double>(R, k + 1, (const double*)r2, nullptr);
       amg_launch(k_add<VT>, dim3(ew_blocks(C.n)), dim3(AMG_BLOCK), 0, R.s, C.n, zc2, e, R.skip);
       R.add(2.0 * sc * nc);
-      R.add(row_pass(C, val_bytes(C)) + 3.0 * sc * nc);
+      R.add(row_pass(C, val_bytes(C), C.pat) + 3.0 * sc * nc);
       R.add(3.0 * sc * nc);
       zc = e;
     }
@@ -1104,7 +1153,7 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out, bool firs
         resid_done = true;
       } else {
         launch_sweep<MT, VT, VT>(R.s, L, vals, dinv, r, cur, nxt, R.skip, h->dev_flags);
-        R.add(row_pass(L, sv) + 4.0 * sx * n);
+        R.add(row_pass(L, sv, L.pat) + 4.0 * sx * n);
         cur = nxt;
         --left;
       }
@@ -1120,7 +1169,7 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out, bool firs
   // residual, restriction, coarse correction, prolongation
   if (!resid_done) {
     launch_resid<MT, VT>(R.s, L, vals, r, cur, t, R.skip, h->dev_flags);
-    R.add(row_pass(L, sv) + 3.0 * sx * n);
+    R.add(row_pass(L, sv, L.pat) + 3.0 * sx * n);
   }
   rec_child<VT>(R, k, t, cur);
   // post-smoothing
@@ -1147,7 +1196,7 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out, bool firs
     }
     if (sw == post - 1 && final_out) {
       launch_sweep<MT, VT, double>(R.s, L, vals, dinv, r, cur, final_out, R.skip, h->dev_flags);
-      R.add(row_pass(L, sv) + 3.0 * sx * n + 8.0 * n);
+      R.add(row_pass(L, sv, L.pat) + 3.0 * sx * n + 8.0 * n);
       return nullptr;
     }
     if (sw == post - 1 && pro &&
@@ -1156,7 +1205,7 @@ static VT* rec_level(VRec& R, int k, const RT* rin, double* final_out, bool firs
       R.add(row_pass(L, sv) + 4.0 * sx * n + prolong_fused_bytes(*pro->F, L));
     } else {
       launch_sweep<MT, VT, VT>(R.s, L, vals, dinv, r, cur, nxt, R.skip, h->dev_flags);
-      R.add(row_pass(L, sv) + 4.0 * sx * n);
+      R.add(row_pass(L, sv, L.pat) + 4.0 * sx * n);
     }
     cur = nxt;
   }
@@ -1178,7 +1227,7 @@ static void record_vcycle(VRec& R, const double* r, double* w) {
 
 // algorithmic bytes of the outer kernels: SpMV + dots reads A, gathers w,
 // writes v, reads r and q; the axpys read w v d q u r and write d q u r
-static double bytes_spmv_dots(const Level& L) { return row_pass(L, 8.0) + 32.0 * L.n; }
+static double bytes_spmv_dots(const Level& L) { return row_pass(L, 8.0, L.patd) + 32.0 * L.n; }
 static double bytes_axpy(const Level& L) { return 80.0 * L.n; }
 
 static void record_iteration(VRec& R, bool precond) {
@@ -1212,8 +1261,8 @@ extern "C" amg_status amg_kernel_bytes(const amg_handle* h, int32_t which, int32
   const double n = L.n, sx = vec_bytes(L), sv = val_bytes(L);
   const bool last = level == h->nl - 1;
   switch (which) {
-    case 0: *bytes = row_pass(L, sv) + 4.0 * sx * n; return AMG_OK;
-    case 1: *bytes = row_pass(L, sv) + 3.0 * sx * n; return AMG_OK;
+    case 0: *bytes = row_pass(L, sv, L.pat) + 4.0 * sx * n; return AMG_OK;
+    case 1: *bytes = row_pass(L, sv, L.pat) + 3.0 * sx * n; return AMG_OK;
     case 2:
     case 3: {
       if (last) return AMG_ERR_INVALID_ARG;

@@ -1,0 +1,187 @@
+"""Pattern-coded columns: the row kernels of a level whose rows fall into at most
+255 tuples of column offsets read a one-byte tuple id per row instead of the
+column indices.  Same entries in the same order and the same arithmetic as the
+CSR form, so every row pass, and so the V-cycle, is bitwise that of the CSR
+form (AMG_PAT=0).  The pattern forms' smaller stages let more blocks share a
+multiprocessor, so the persistent outer kernel runs another number of blocks
+and its dot products add their block partial sums in another (fixed) order:
+the solves agree to rounding, at the oracle's bars.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2303_02352_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_02352_gb300 import build
+    build.build()
+    from paper_2303_02352_gb300 import amg
+    return amg.load()
+
+
+def G(A, **kw):
+    from paper_2303_02352_gb300 import amg
+    return amg.Hierarchy(A, **kw)
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def csr_from_coo(n, r, c, v):
+    order = np.lexsort((c, r))
+    r, c, v = r[order], c[order], v[order]
+    rp = np.zeros(n + 1, dtype=np.int32)
+    np.add.at(rp, r + 1, 1)
+    return W.CSR(n, np.cumsum(rp).astype(np.int32), c.astype(np.int32), v)
+
+
+def block_diagonal(sizes, periods):
+    """Dense blocks k x k (diagonal k, off-diagonal -1: symmetric, strictly
+    diagonally dominant), the sequence `sizes` repeated `periods` times.  Row r
+    of a block of size k has the column offsets (-r, ..., k-1-r), so the matrix
+    has exactly sum(set(sizes)) distinct offset tuples."""
+    rows, cols, vals = [], [], []
+    base = 0
+    for _ in range(periods):
+        for k in sizes:
+            idx = np.arange(base, base + k)
+            rr, cc = np.meshgrid(idx, idx, indexing="ij")
+            rows.append(rr.ravel())
+            cols.append(cc.ravel())
+            vals.append(np.where(rr == cc, float(k), -1.0).ravel())
+            base += k
+    return csr_from_coo(base, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def paired_rows(dmax, singleton, periods):
+    """Rows coupled in pairs at distance d = 1 .. dmax (a block of 2d rows: row
+    j with row j + d; diagonal 2, coupling -1), with one uncoupled row per
+    period if `singleton`: 2 dmax (+ 1) distinct offset tuples of at most two
+    entries, (0, d) and (-d, 0) (and (0,))."""
+    rows, cols, vals = [], [], []
+    base = 0
+    for _ in range(periods):
+        for d in range(1, dmax + 1):
+            a = np.arange(base, base + d)
+            rows += [a, a + d, a, a + d]
+            cols += [a, a + d, a + d, a]
+            vals += [np.full(d, 2.0), np.full(d, 2.0), np.full(d, -1.0), np.full(d, -1.0)]
+            base += 2 * d
+        if singleton:
+            rows.append(np.array([base]))
+            cols.append(np.array([base]))
+            vals.append(np.array([1.0]))
+            base += 1
+    return csr_from_coo(base, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+STENCILS = {
+    "poisson40": lambda: W.poisson7(40),                 # 64,000 rows, 27 tuples
+    "diff27_40": lambda: W.diffusion27(40, 2.0, 3),      # 27 tuples, 64-row tiles with 4 threads per row
+    "diff7_48": lambda: W.diffusion7(48, 2.0, 1001),
+}
+
+
+@pytest.mark.parametrize("name", sorted(STENCILS))
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_pattern_form_is_bitwise_the_csr_form(name, prec, monkeypatch):
+    A = STENCILS[name]()
+    g = G(A, precision=prec)
+    info = g.info()
+    # a 7- or 27-point stencil on an N^3 grid: 3 cases per axis (low face, interior, high face)
+    assert info["column_patterns"][0] == 27 and info["outer_patterns"] == 27
+    monkeypatch.setenv("AMG_PAT", "0")
+    c = G(A, precision=prec)
+    ic = c.info()
+    assert all(p == 0 for p in ic["column_patterns"]) and ic["outer_patterns"] == 0
+    assert info["n"] == ic["n"] and info["nnz"] == ic["nnz"]
+    # the pattern form moves one id byte per row instead of four index bytes per entry
+    assert info["vcycle_bytes"] < ic["vcycle_bytes"]
+    r = W.random_vector(A.n, 8)
+    zg, zc = g.vcycle(r).cpu().numpy(), c.vcycle(r).cpu().numpy()
+    assert np.array_equal(zg, zc)
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 9))
+    rg, rc = g.pcg_solve(b), c.pcg_solve(b)
+    assert rg["status"] == 0 and rg["true_rel_res"] < 1e-6 and abs(rg["iters"] - rc["iters"]) <= 1
+    m = min(rg["iters"], rc["iters"])
+    xg = g.pcg_solve(b, tol=0.0, maxit=m)["x"].cpu().numpy()
+    xc = c.pcg_solve(b, tol=0.0, maxit=m)["x"].cpu().numpy()
+    assert rel(xg, xc) < 1e-10
+    if prec == 0:
+        o = O.Hierarchy(A)
+        assert rel(zg, o.vcycle(r)) < 1e-12
+
+
+@pytest.mark.parametrize("name", sorted(STENCILS))
+@pytest.mark.parametrize("prec", [0, 2])
+def test_rows_from_tuple_lengths_equal_rows_from_row_pointers(name, prec, monkeypatch):
+    """Form 2 (AMG_PAT=2; one thread per row: a warp's rows located from one
+    row pointer per 32 rows and the tuple lengths) against the default form 1
+    (row pointers): the same stages and grid, so V-cycle and solve are bitwise
+    equal.  27-point levels run 2-4 threads per row and keep form 1."""
+    A = STENCILS[name]()
+    g = G(A, precision=prec)
+    info = g.info()
+    assert info["column_form"][0] == 1
+    monkeypatch.setenv("AMG_PAT", "2")
+    c = G(A, precision=prec)
+    ic = c.info()
+    two = name != "diff27_40"
+    assert ic["column_form"][0] == (2 if two else 1) and ic["column_patterns"] == info["column_patterns"]
+    if two:  # one row pointer per 32 rows instead of one per row
+        assert ic["vcycle_bytes"] < info["vcycle_bytes"]
+    r = W.random_vector(A.n, 3)
+    assert np.array_equal(g.vcycle(r).cpu().numpy(), c.vcycle(r).cpu().numpy())
+    b = W.rhs_from_solution(A, W.random_vector(A.n, 2))
+    rg, rc = g.pcg_solve(b), c.pcg_solve(b)
+    assert rg["iters"] == rc["iters"] and np.array_equal(rg["x"].cpu().numpy(), rc["x"].cpu().numpy())
+
+
+@pytest.mark.parametrize("dmax, singleton, expect", [(127, True, 255), (128, False, 0)])
+def test_tuple_count_boundary(dmax, singleton, expect, monkeypatch):
+    """255 distinct offset tuples take the pattern form (ids 0 .. 254), 256
+    leave the level on CSR columns; the V-cycle is the oracle's either way."""
+    A = paired_rows(dmax, singleton, 3)
+    assert A.n >= 32768
+    g = G(A)
+    info = g.info()
+    assert info["column_patterns"][0] == expect
+    o = O.Hierarchy(A)
+    r = W.random_vector(A.n, 5)
+    zg = g.vcycle(r).cpu().numpy()
+    assert rel(zg, o.vcycle(r)) < 1e-12
+    monkeypatch.setenv("AMG_PAT", "0")
+    assert np.array_equal(zg, G(A).vcycle(r).cpu().numpy())
+
+
+def test_table_larger_than_the_cap_keeps_csr_columns():
+    """231 tuples of up to 21 entries: 4,851 table entries, above the 1,024 the
+    row kernels hold in shared memory, so the level keeps CSR columns."""
+    A = block_diagonal(list(range(1, 22)), 160)
+    assert A.n >= 32768
+    g = G(A)
+    assert g.info()["column_patterns"][0] == 0
+    o = O.Hierarchy(A)
+    r = W.random_vector(A.n, 4)
+    assert rel(g.vcycle(r).cpu().numpy(), o.vcycle(r)) < 1e-12
+
+
+def test_irregular_level_keeps_csr_columns():
+    """A random sparse graph has more distinct tuples than ids: CSR columns."""
+    A = W.random_spd(40000, 11, max_partners=12)
+    g = G(A)
+    assert g.info()["column_patterns"][0] == 0
+    o = O.Hierarchy(A)
+    r = W.random_vector(A.n, 6)
+    assert rel(g.vcycle(r).cpu().numpy(), o.vcycle(r)) < 1e-12
