@@ -926,12 +926,22 @@ amg_status amg_finish_setup(amg_handle* h) {
       amg_status sp = amg_build_patterns(h, k);
       if (sp != AMG_OK) return sp;
     }
-    auto pat_form = [&](int R, int sb) {  // 2: one thread per row; 1: the other pattern forms
+    // pattern-coded float levels with tiles of 32-128 rows: two consumer groups
+    // with half the threads per row (27-point 128^3 FP32 level-0 sweep 75.4 ->
+    // 56.4 us, solve 17.3 -> 16.0 ms; on FP64 levels the form is mixed and
+    // stays off, use_ng above)
+    if (h->use_ng >= 1 && L.pid && vb < 8 && L.pipe && L.sb == 1 && L.R >= 32 && L.R <= 128) L.sb = 6;
+    // FP64 forms with several threads per row (27-point levels) keep CSR
+    // columns: FP64-issue bound, their kernels gain nothing from fewer bytes
+    // (27-point 128^3 sweep 166 vs 163 us) and the V-cycle measured slower
+    // (1.94 vs 1.74 ms)
+    auto pat_form = [&](int R, int sb, int value_bytes) {  // 2: one thread per row; 1: the other pattern forms
       if ((sb == 1 && R == 256) || (sb == 6 && R == 128)) return h->use_pat >= 2 ? 2 : 1;
+      if (value_bytes == 8) return 0;
       return ((sb == 1 && R >= 64) || sb == 6) ? 1 : 0;
     };
-    L.pat = L.pid && L.pipe ? pat_form(L.R, L.sb) : 0;
-    L.patd = L.pid && L.piped ? pat_form(L.Rd, L.sbd) : 0;
+    L.pat = L.pid && L.pipe ? pat_form(L.R, L.sb, vb) : 0;
+    L.patd = L.pid && L.piped ? pat_form(L.Rd, L.sbd, 8) : 0;
     AMG_ALLOC(h, L.l1, double, L.n);
     AMG_ALLOC(h, L.dinv, double, L.n);
     if (L.lowp) {

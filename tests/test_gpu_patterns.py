@@ -1,8 +1,9 @@
 """Pattern-coded columns: the row kernels of a level whose rows fall into at most
 255 tuples of column offsets read a one-byte tuple id per row instead of the
 column indices.  Same entries in the same order and the same arithmetic as the
-CSR form, so every row pass, and so the V-cycle, is bitwise that of the CSR
-form (AMG_PAT=0).  The pattern forms' smaller stages let more blocks share a
+CSR form, so every row pass of the same kernel form, and so the V-cycle, is
+bitwise that of the CSR form (AMG_PAT=0); pattern-coded float levels with
+short tiles also take the two-group form, which sums a row in another order.  The pattern forms' smaller stages let more blocks share a
 multiprocessor, so the persistent outer kernel runs another number of blocks
 and its dot products add their block partial sums in another (fixed) order:
 the solves agree to rounding, at the oracle's bars.
@@ -93,6 +94,12 @@ STENCILS = {
 }
 
 
+def expected_form(name, prec):
+    """Column form of level 0's V-cycle kernels: FP64 levels whose rows take
+    several threads (27-point) keep CSR columns, the others use form 1."""
+    return 0 if (name == "diff27_40" and prec == 0) else 1
+
+
 @pytest.mark.parametrize("name", sorted(STENCILS))
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_pattern_form_is_bitwise_the_csr_form(name, prec, monkeypatch):
@@ -100,24 +107,35 @@ def test_pattern_form_is_bitwise_the_csr_form(name, prec, monkeypatch):
     g = G(A, precision=prec)
     info = g.info()
     # a 7- or 27-point stencil on an N^3 grid: 3 cases per axis (low face, interior, high face)
-    assert info["column_patterns"][0] == 27 and info["outer_patterns"] == 27
+    form = expected_form(name, prec)
+    assert info["column_form"][0] == form and info["column_patterns"][0] == (27 if form else 0)
+    assert info["outer_patterns"] == (0 if name == "diff27_40" else 27)
     monkeypatch.setenv("AMG_PAT", "0")
     c = G(A, precision=prec)
     ic = c.info()
     assert all(p == 0 for p in ic["column_patterns"]) and ic["outer_patterns"] == 0
     assert info["n"] == ic["n"] and info["nnz"] == ic["nnz"]
     # the pattern form moves one id byte per row instead of four index bytes per entry
-    assert info["vcycle_bytes"] < ic["vcycle_bytes"]
+    if form:
+        assert info["vcycle_bytes"] < ic["vcycle_bytes"]
     r = W.random_vector(A.n, 8)
     zg, zc = g.vcycle(r).cpu().numpy(), c.vcycle(r).cpu().numpy()
-    assert np.array_equal(zg, zc)
+    if info["consumer_groups"] == ic["consumer_groups"]:
+        assert np.array_equal(zg, zc)
+    else:
+        # pattern-coded float levels with short tiles take the two-group form
+        # (half the threads per row): another order of each row's float sum
+        assert name == "diff27_40" and prec > 0 and info["consumer_groups"][0] == 2
+        assert rel(zg, zc) < 1e-6
     b = W.rhs_from_solution(A, W.random_vector(A.n, 9))
     rg, rc = g.pcg_solve(b), c.pcg_solve(b)
     assert rg["status"] == 0 and rg["true_rel_res"] < 1e-6 and abs(rg["iters"] - rc["iters"]) <= 1
     m = min(rg["iters"], rc["iters"])
     xg = g.pcg_solve(b, tol=0.0, maxit=m)["x"].cpu().numpy()
     xc = c.pcg_solve(b, tol=0.0, maxit=m)["x"].cpu().numpy()
-    assert rel(xg, xc) < 1e-10
+    # the bars of the oracle comparisons: 1e-10 for FP64, and for float
+    # hierarchies that round in another order 1e-9 (test_gpu_parity.py)
+    assert rel(xg, xc) < (1e-10 if prec == 0 else 1e-9)
     if prec == 0:
         o = O.Hierarchy(A)
         assert rel(zg, o.vcycle(r)) < 1e-12
@@ -129,16 +147,17 @@ def test_rows_from_tuple_lengths_equal_rows_from_row_pointers(name, prec, monkey
     """Form 2 (AMG_PAT=2; one thread per row: a warp's rows located from one
     row pointer per 32 rows and the tuple lengths) against the default form 1
     (row pointers): the same stages and grid, so V-cycle and solve are bitwise
-    equal.  27-point levels run 2-4 threads per row and keep form 1."""
+    equal.  27-point levels run 2-4 threads per row and keep their form."""
     A = STENCILS[name]()
     g = G(A, precision=prec)
     info = g.info()
-    assert info["column_form"][0] == 1
+    assert info["column_form"][0] == expected_form(name, prec)
     monkeypatch.setenv("AMG_PAT", "2")
     c = G(A, precision=prec)
     ic = c.info()
     two = name != "diff27_40"
-    assert ic["column_form"][0] == (2 if two else 1) and ic["column_patterns"] == info["column_patterns"]
+    assert ic["column_form"][0] == (2 if two else expected_form(name, prec))
+    assert ic["column_patterns"] == info["column_patterns"]
     if two:  # one row pointer per 32 rows instead of one per row
         assert ic["vcycle_bytes"] < info["vcycle_bytes"]
     r = W.random_vector(A.n, 3)
