@@ -178,6 +178,11 @@ def peaks():
 KERNEL_SOURCES = ("rows.cuh", "amg_internal.cuh")
 
 
+# nominal dense FP64 rate of one GB300 (2 multiply-adds per clock per
+# multiprocessor, 152 multiprocessors, 2.07 GHz)
+FP64_TFLOPS = 1.25
+
+
 def kernel_digest() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2303_02352_gb300", "csrc")
@@ -360,6 +365,7 @@ def main():
     peak, peak_kind = peaks()
     t_sweep = g.time_kernel(amg.K_SWEEP, 0, reps=50)
     by_sweep = g.kernel_bytes(amg.K_SWEEP, 0)
+    fp64_flop = 2.0 * (info["nnz"][0] + info["n"][0]) if args.precision == "fp64" else 0.0
     ach = by_sweep / (t_sweep * 1e-3) / 1e9
     t_vc = g.time_vcycle(reps=20)
     vc_gbs = info["vcycle_bytes"] / (t_vc * 1e-3) / 1e9
@@ -482,6 +488,12 @@ def main():
                                                 info["stage_scale"][0], info["column_patterns"][0]),
                          "kernel": "l1-Jacobi sweep, level 0", "algorithmic_bytes_per_launch": by_sweep,
                          "launch_ms": round(t_sweep, 5), "peak_kind": peak_kind},
+            # the same launch against the FP64 issue rate: one multiply-add per
+            # entry and one per row (FP64 levels; 0 for float levels)
+            "co_limit": {"bound": "fp64", "unit": "TFLOP/s", "peak": FP64_TFLOPS, "peak_kind": "nominal",
+                         "flop_per_launch": fp64_flop,
+                         "achieved": round(fp64_flop / (t_sweep * 1e-3) / 1e12, 4),
+                         "frac": round(fp64_flop / (t_sweep * 1e-3) / 1e12 / FP64_TFLOPS, 4)},
             "vcycle": {"ms": round(t_vc, 4), "bytes": info["vcycle_bytes"], "GB/s": round(vc_gbs, 1),
                        "frac": round(vc_gbs / peak, 4), "launches": info["vcycle_launches"]},
             "kernels_level0": kernels,
