@@ -25,20 +25,24 @@
 // kernels need)
 // SB scales the stage: SB = 4 (FP64 only) holds 256 rows of up to 32 entries,
 // so long-row levels keep one thread per row (see launch_rows)
-// SMALL (pattern-coded columns): the same value capacity, and room for the
-// tile's one-byte row ids instead of its column indices; the smaller stage
-// lets more blocks share a multiprocessor (FP64: six instead of four)
-template <typename MT, int SB = 1, bool PAT = false>
+// SMALL (pattern-coded columns): the same value capacity, room for the tile's
+// one-byte row ids instead of its column indices, and for the tile's row
+// pointers and up to three row vectors of VB bytes per entry (iterate,
+// right-hand side, D) of its RT rows, so that every stream of the row pass
+// arrives by bulk copy ahead of the consumers
+template <typename MT, int SB = 1, bool PAT = false, int VB = 8, int RT = PIPE_CONSUMERS>
 struct PipeTile {
   static constexpr int VE = 16 / (int)sizeof(MT);
   static constexpr int CAP = amg_pipe_tile_bytes((int)sizeof(MT)) * SB / ((int)sizeof(MT) + 4);
   MT v[CAP + 2 * VE];
   int32_t c[PAT ? (PIPE_CONSUMERS + 16) / 4 : CAP + 8];
+  int32_t rps[PAT ? RT + 8 : 4];
+  alignas(16) unsigned char ov[PAT ? 3 * RT * VB : 16];
 };
 
-template <typename MT, int S, int SB = 1, bool PAT = false>
+template <typename MT, int S, int SB = 1, bool PAT = false, int VB = 8, int RT = PIPE_CONSUMERS>
 struct PipeSmem {
-  PipeTile<MT, SB, PAT> st[S];
+  PipeTile<MT, SB, PAT, VB, RT> st[S];
   unsigned long long full[S];   // producer -> consumers: the stage holds the tile
   unsigned long long empty[S];  // consumers -> producer: every consumer warp has read it
 };
@@ -146,6 +150,7 @@ struct RowArgs {
   const int32_t* plen;  // entries of each tuple (npat)
   int npat;
   const int32_t* pcb;   // PAT = 2: row_ptr at every 32nd row, and nnz
+  int stage_rows;       // small-stage pattern forms: row pointers and row vectors by bulk copy (16-byte aligned)
 };
 
 
@@ -226,8 +231,17 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
   pdl_trigger();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   constexpr bool SMALL = pat_small<MT, MODE, PAT>();
-  auto* P = reinterpret_cast<PipeSmem<MT, S, SB, SMALL>*>(smem_raw);
-  int32_t* tab = reinterpret_cast<int32_t*>(smem_raw + sizeof(PipeSmem<MT, S, SB, SMALL>));  // PAT: offsets, lengths
+  constexpr int VB = (int)sizeof(VT);
+  // staged row data of the small-stage forms: the row pointers (form 1) and
+  // the row vectors the mode reads per row (slot 0 iterate, 1 right-hand
+  // side or b, 2 D)
+  constexpr int NV = !SMALL ? 0
+                     : MODE == PM_SWEEP ? 3
+                     : (MODE == PM_RESID || MODE == PM_RINIT || MODE == PM_RTRUE || MODE == PM_RNORM) ? 1 : 0;
+  constexpr bool SRP = SMALL && PAT == 1;
+  const bool stg = (SRP || NV > 0) && a.stage_rows != 0;
+  auto* P = reinterpret_cast<PipeSmem<MT, S, SB, SMALL, VB, R>*>(smem_raw);
+  int32_t* tab = reinterpret_cast<int32_t*>(smem_raw + sizeof(PipeSmem<MT, S, SB, SMALL, VB, R>));  // PAT: offsets, lengths
   __shared__ double red[96];
   constexpr int VE = PipeTile<MT>::VE;
   constexpr int NCW = PIPE_CONSUMERS / 32;  // consumer warps
@@ -252,7 +266,27 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
   // copies of this block's k-th tile (producer lane only); the matrix does not
   // change during a solve, so the first S tiles are requested before waiting
   // for the previous kernel
-  auto issue = [&](int k, int stage) {
+  // the row vectors of this block's k-th tile (they change from kernel to
+  // kernel: requested only after the wait on the previous kernel)
+  auto issue_vectors = [&](int k, int stage) {
+    if constexpr (NV > 0) {
+      if (!stg) return;
+      const int tile = blockIdx.x + k * G;
+      const int row0 = tile * R, row1 = min(row0 + R, n);
+      const uint32_t nb = (uint32_t)(((row1 - row0) * VB + 15) & ~15);
+      unsigned char* ov = P->st[stage].ov;
+      if constexpr (MODE == PM_SWEEP) {
+        tma_load_1d(ov, a.x + row0, nb, &P->full[stage]);
+        tma_load_1d(ov + R * VB, a.r + row0, nb, &P->full[stage]);
+        tma_load_1d(ov + 2 * R * VB, a.dinv + row0, nb, &P->full[stage]);
+      } else if constexpr (MODE == PM_RESID) {
+        tma_load_1d(ov + R * VB, a.r + row0, nb, &P->full[stage]);
+      } else {
+        tma_load_1d(ov + R * VB, a.b + row0, nb, &P->full[stage]);
+      }
+    }
+  };
+  auto issue = [&](int k, int stage, bool with_vectors) {
     const int tile = blockIdx.x + k * G;
     const int row0 = tile * R, row1 = min(row0 + R, n);
     // row0 is a multiple of 32 and row1 one or n
@@ -263,10 +297,16 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
     // PAT: the ids of rows row0 .. row1-1 (row0 is a multiple of R >= 32, so
     // the source is 16-byte aligned; the allocation is padded past n)
     const uint32_t bc = PAT > 0 ? (uint32_t)((row1 - row0 + 15) & ~15) : (uint32_t)(((p1 - ac) * 4 + 15) & ~15);
-    mbar_expect_tx(&P->full[stage], bv + bc);
+    // staged row data: row pointers row0 .. row1 and NV vectors (all sources
+    // 16-byte aligned, allocations padded past their end)
+    const uint32_t brp = (SRP && stg) ? (uint32_t)(((row1 - row0 + 1) * 4 + 15) & ~15) : 0u;
+    const uint32_t bvec = (NV > 0 && stg) ? (uint32_t)NV * (uint32_t)(((row1 - row0) * VB + 15) & ~15) : 0u;
+    mbar_expect_tx(&P->full[stage], bv + bc + brp + bvec);
     tma_load_1d(P->st[stage].v, a.v + av, bv, &P->full[stage]);
     if constexpr (PAT > 0) tma_load_1d(P->st[stage].c, a.pid + row0, bc, &P->full[stage]);
     else tma_load_1d(P->st[stage].c, a.ci + ac, bc, &P->full[stage]);
+    if (brp) tma_load_1d(P->st[stage].rps, a.rp + row0, brp, &P->full[stage]);
+    if (with_vectors) issue_vectors(k, stage);
   };
   const bool producer = warp == NCW && lane == 0;
   int issued = 0;
@@ -274,9 +314,11 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
   constexpr bool early = MODE != PM_RTRUE;
   if (!early) pdl_wait();
   if (early && producer)
-    for (; issued < S && blockIdx.x + issued * G < ntiles; ++issued) issue(issued, issued);
+    for (; issued < S && blockIdx.x + issued * G < ntiles; ++issued) issue(issued, issued, false);
 
   if (early) pdl_wait();  // the previous kernel's results (vectors, flags) are visible from here on
+  if (early && producer)  // the row vectors of the tiles requested early
+    for (int k = 0; k < issued; ++k) issue_vectors(k, k);
   bool skip = false;
   if constexpr (MODE == PM_SWEEP || MODE == PM_RESID || MODE == PM_SWEEP_PROLONG) skip = *a.skip != 0;
   else if constexpr (MODE == PM_DOTS) skip = a.st->done != 0;
@@ -287,7 +329,7 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
     return;
   }
   if (!early && producer)
-    for (; issued < S && blockIdx.x + issued * G < ntiles; ++issued) issue(issued, issued);
+    for (; issued < S && blockIdx.x + issued * G < ntiles; ++issued) issue(issued, issued, true);
 
   double acc[3] = {0.0, 0.0, 0.0};
   const bool first = (MODE == PM_DOTS) ? (a.st->it == 0) : false;
@@ -306,7 +348,7 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
           aborted = true;
           break;
         }
-        issue(k, stage);
+        issue(k, stage, true);
       }
       if (aborted) {  // drain: the last copy issued into each stage, bounded
         for (int j = 1; j <= S && k - j >= 0; ++j) {
@@ -328,19 +370,22 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
       const int row = row0 + tg / TPR;
       const bool live = row < row1;
       const bool lead = live && sub == 0;      // the lane that finishes the row
-      const int p0 = CB ? __ldg(&a.pcb[row0 >> 5]) : __ldg(&a.rp[row0]);
+      const bool rows_staged = SRP && stg;  // row pointers from the stage (after the wait)
+      const bool vecs_staged = NV > 0 && stg;  // row vectors from the stage
+      int p0 = 0;
+      if (!rows_staged) p0 = CB ? __ldg(&a.pcb[row0 >> 5]) : __ldg(&a.rp[row0]);
       int q0 = 0, q1 = 0, qs = 0;
       VT own = 0, rr = 0, dd = 0, qq = 0;
       OT zn = 0;  // PM_SWEEP_PROLONG: the row's new value
       int wbase = 0;  // CB: first entry of the warp's first row
       if constexpr (CB) {
         if (row - lane < n) wbase = __ldg(&a.pcb[(row - lane) >> 5]);
-      } else if (live) {
+      } else if (live && !rows_staged) {
         qs = __ldg(&a.rp[row]);
         q0 = qs + sub;
         q1 = __ldg(&a.rp[row + 1]);
       }
-      if (lead) {
+      if (lead && !vecs_staged) {
         if constexpr (MODE == PM_SWEEP || MODE == PM_SWEEP_PROLONG) {
           own = __ldg(&a.x[row]);
           rr = __ldg(&a.r[row]);
@@ -359,8 +404,29 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
         if (lane == 0) atomicOr(a.flags, ST_TIMEOUT);
         break;
       }
+      const PipeTile<MT, SB, SMALL, VB, R>& T = P->st[stage];
+      if (rows_staged) {
+        p0 = T.rps[0];
+        if (live) {
+          qs = T.rps[row - row0];
+          q0 = qs + sub;
+          q1 = T.rps[row - row0 + 1];
+        }
+      }
+      if constexpr (NV > 0) {
+        if (vecs_staged && lead) {
+          const VT* ov = reinterpret_cast<const VT*>(T.ov);
+          const int j = row - row0;
+          if constexpr (MODE == PM_SWEEP) {
+            own = ov[j];
+            rr = ov[R + j];
+            dd = ov[2 * R + j];
+          } else {
+            rr = ov[R + j];
+          }
+        }
+      }
       const int av = p0 & ~(VE - 1), ac = p0 & ~3;
-      const PipeTile<MT, SB, SMALL>& T = P->st[stage];
       // residuals, and sweeps in standard stages, accumulate
       // r_i - sum_j a_ij x_j from r_i (the lead lane holds r_i, the others 0):
       // one FP64 operation per row fewer than summing first and subtracting, on
@@ -468,14 +534,14 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
 
 // dynamic shared memory of a pipelined row kernel: the stages and barriers,
 // and for the pattern forms the offset table (16-byte granules)
-template <typename MT, int S, int SB, int MODE, int PAT>
+template <typename MT, typename VT, int S, int SB, int MODE, int PAT, int R>
 static constexpr int pipe_smem(int tab_n) {
-  return (int)sizeof(PipeSmem<MT, S, SB, pat_small<MT, MODE, PAT>()>) + (PAT > 0 ? ((tab_n * 4 + 15) & ~15) : 0);
+  return (int)sizeof(PipeSmem<MT, S, SB, pat_small<MT, MODE, PAT>(), (int)sizeof(VT), R>) +
+         (PAT > 0 ? ((tab_n * 4 + 15) & ~15) : 0);
 }
 
 // grid of a persistent pipelined kernel: one wave of resident blocks, at most
 // one block per tile
-
 template <int TPR, int S, int MODE, typename MT, typename VT, typename OT, int SB = 1, int NG = 1, int PAT = 0>
 static int pipe_grid(int n, int tab_n = 0) {
   // resident blocks per multiprocessor, by table size in 256-byte steps
@@ -484,14 +550,14 @@ static int pipe_grid(int n, int tab_n = 0) {
   constexpr int R = PIPE_CONSUMERS / NG / TPR;
   auto kern = k_rows_pipe<TPR, S, MODE, MT, VT, OT, SB, NG, PAT>;
   if (!attr) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pipe_smem<MT, S, SB, MODE, PAT>(PAT_TAB_MAX));
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pipe_smem<MT, VT, S, SB, MODE, PAT, R>(PAT_TAB_MAX));
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr = true;
   }
   int& bps = bps_by[PAT > 0 ? (tab_n * 4 + 255) / 256 : 0];
   if (bps <= 0) {  // sized for the table rounded up to its 256-byte step
     int b = 0;
-    const size_t occ = sizeof(PipeSmem<MT, S, SB, pat_small<MT, MODE, PAT>()>) +
+    const size_t occ = sizeof(PipeSmem<MT, S, SB, pat_small<MT, MODE, PAT>(), (int)sizeof(VT), R>) +
                        (PAT > 0 ? (size_t)((tab_n * 4 + 255) & ~255) : 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, PIPE_CONSUMERS + 32, occ);
     bps = b < 1 ? 1 : b;
@@ -503,9 +569,10 @@ static int pipe_grid(int n, int tab_n = 0) {
 
 template <int TPR, int S, int MODE, typename MT, typename VT, typename OT, int SB = 1, int NG = 1, int PAT = 0>
 static void launch_pipe(cudaStream_t s, const RowArgs<MT, VT, OT>& a) {
+  constexpr int R = PIPE_CONSUMERS / NG / TPR;
   const int tab_n = PAT > 0 ? a.ptab_n + a.npat : 0;  // offsets, then lengths
   const int grid = pipe_grid<TPR, S, MODE, MT, VT, OT, SB, NG, PAT>(a.n, tab_n);
-  const int smem = pipe_smem<MT, S, SB, MODE, PAT>(tab_n);
+  const int smem = pipe_smem<MT, VT, S, SB, MODE, PAT, R>(tab_n);
   amg_launch(k_rows_pipe<TPR, S, MODE, MT, VT, OT, SB, NG, PAT>, dim3(grid), dim3(PIPE_CONSUMERS + 32), (size_t)smem, s,
              a);
 }

@@ -572,13 +572,18 @@ template <int MODE, typename MT, typename VT, typename OT>
 static void launch_rows(cudaStream_t s, int R, int sb, const RowArgs<MT, VT, OT>& a) {
   if constexpr (MODE != PM_SWEEP_PROLONG) {  // latency-bound levels only: no pattern form
     if (a.pid) {
-      if (a.pcb) {  // one thread per row: R = 128 in two groups, or R = 256
-        if (sb == 6) launch_pipe<1, 4, MODE, MT, VT, OT, 1, 2, 2>(s, a);
-        else launch_pipe<1, 2, MODE, MT, VT, OT, 1, 1, 2>(s, a);
+      // small-stage forms move the row pointers and row vectors by bulk copy
+      // where every source is 16-byte aligned (the library's own buffers are)
+      RowArgs<MT, VT, OT> b = a;
+      auto al = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+      b.stage_rows = al(a.rp) && al(a.x) && al(a.r) && al(a.dinv) && al(a.b);
+      if (b.pcb) {  // one thread per row: R = 128 in two groups, or R = 256
+        if (sb == 6) launch_pipe<1, 4, MODE, MT, VT, OT, 1, 2, 2>(s, b);
+        else launch_pipe<1, 2, MODE, MT, VT, OT, 1, 1, 2>(s, b);
       } else if (sb == 6) {
-        DISPATCH_NG(R, (launch_pipe<TP, 4, MODE, MT, VT, OT, 1, 2, 1>(s, a)));
+        DISPATCH_NG(R, (launch_pipe<TP, 4, MODE, MT, VT, OT, 1, 2, 1>(s, b)));
       } else {
-        DISPATCH_TPR_PAT(PIPE_CONSUMERS / R, (launch_pipe<TP, 2, MODE, MT, VT, OT, 1, 1, 1>(s, a)));
+        DISPATCH_TPR_PAT(PIPE_CONSUMERS / R, (launch_pipe<TP, 2, MODE, MT, VT, OT, 1, 1, 1>(s, b)));
       }
       return;
     }
