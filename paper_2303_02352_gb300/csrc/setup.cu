@@ -940,6 +940,7 @@ amg_status amg_finish_setup(amg_handle* h) {
       if (value_bytes == 8) return 0;
       return ((sb == 1 && R >= 64) || sb == 6) ? 1 : 0;
     };
+    L.stage_rows = h->use_stage != 0;
     L.pat = L.pid && L.pipe ? pat_form(L.R, L.sb, vb) : 0;
     L.patd = L.pid && L.piped ? pat_form(L.Rd, L.sbd, 8) : 0;
     AMG_ALLOC(h, L.l1, double, L.n);
@@ -989,7 +990,8 @@ void amg_read_hooks(amg_handle* h) {
   // AMG_SMALL_ROWS, AMG_MIN_TPR row-kernel forms,
   // AMG_PAT=0/1 CSR columns on every level / pattern-coded columns located
   // by row pointers only (AMG_PAT=2: rows located from the tuple lengths
-  // where one thread takes a row),
+  // where one thread takes a row), AMG_STAGE=0 row data of the small-stage
+  // pattern kernels loaded by the consumers instead of staged,
   // AMG_SUITOR_CAP step cap of the matching loop,
   // AMG_FAIL_ALLOC_AFTER make the k-th device allocation of the handle fail
   if (const char* e = getenv("AMG_SUITOR_CAP")) h->suitor_cap = atoll(e);
@@ -1004,6 +1006,7 @@ void amg_read_hooks(amg_handle* h) {
   if (const char* e = getenv("AMG_PIPE")) h->use_pipe = atoi(e);
   if (const char* e = getenv("AMG_NG")) h->use_ng = atoi(e);
   if (const char* e = getenv("AMG_PAT")) h->use_pat = atoi(e);
+  if (const char* e = getenv("AMG_STAGE")) h->use_stage = atoi(e);
 }
 
 extern "C" amg_status amg_setup(const amg_csr* A, const amg_params* p, void* stream, amg_handle** out) {

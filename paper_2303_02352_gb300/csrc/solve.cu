@@ -563,6 +563,7 @@ static inline void use_patterns(RowArgs<MT, VT, OT>& a, const Level& L, int form
   a.plen = L.plen;
   a.npat = L.npat;
   a.pcb = form == 2 ? L.pcb : nullptr;
+  a.stage_rows = L.stage_rows ? 1 : 0;
 }
 
 // sb = 2 / 4: FP64 level with long rows in 2x / 4x stages (R = 128 with two
@@ -576,7 +577,7 @@ static void launch_rows(cudaStream_t s, int R, int sb, const RowArgs<MT, VT, OT>
       // where every source is 16-byte aligned (the library's own buffers are)
       RowArgs<MT, VT, OT> b = a;
       auto al = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
-      b.stage_rows = al(a.rp) && al(a.x) && al(a.r) && al(a.dinv) && al(a.b);
+      b.stage_rows = a.stage_rows && al(a.rp) && al(a.x) && al(a.r) && al(a.dinv) && al(a.b);
       if (b.pcb) {  // one thread per row: R = 128 in two groups, or R = 256
         if (sb == 6) launch_pipe<1, 4, MODE, MT, VT, OT, 1, 2, 2>(s, b);
         else launch_pipe<1, 2, MODE, MT, VT, OT, 1, 1, 2>(s, b);
