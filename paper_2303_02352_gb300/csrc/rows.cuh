@@ -30,19 +30,20 @@
 // pointers and up to three row vectors of VB bytes per entry (iterate,
 // right-hand side, D) of its RT rows, so that every stream of the row pass
 // arrives by bulk copy ahead of the consumers
-template <typename MT, int SB = 1, bool PAT = false, int VB = 8, int RT = PIPE_CONSUMERS>
+// (STG: the stage has the row-data area; PAT: the column area holds row ids)
+template <typename MT, int SB = 1, bool PAT = false, int VB = 8, int RT = PIPE_CONSUMERS, bool STG = PAT>
 struct PipeTile {
   static constexpr int VE = 16 / (int)sizeof(MT);
   static constexpr int CAP = amg_pipe_tile_bytes((int)sizeof(MT)) * SB / ((int)sizeof(MT) + 4);
   MT v[CAP + 2 * VE];
   int32_t c[PAT ? (PIPE_CONSUMERS + 16) / 4 : CAP + 8];
-  int32_t rps[PAT ? RT + 8 : 4];
-  alignas(16) unsigned char ov[PAT ? 3 * RT * VB : 16];
+  int32_t rps[STG ? RT + 8 : 4];
+  alignas(16) unsigned char ov[STG ? 3 * RT * VB : 16];
 };
 
-template <typename MT, int S, int SB = 1, bool PAT = false, int VB = 8, int RT = PIPE_CONSUMERS>
+template <typename MT, int S, int SB = 1, bool PAT = false, int VB = 8, int RT = PIPE_CONSUMERS, bool STG = PAT>
 struct PipeSmem {
-  PipeTile<MT, SB, PAT, VB, RT> st[S];
+  PipeTile<MT, SB, PAT, VB, RT, STG> st[S];
   unsigned long long full[S];   // producer -> consumers: the stage holds the tile
   unsigned long long empty[S];  // consumers -> producer: every consumer warp has read it
 };
@@ -70,6 +71,15 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
 
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
   uint32_t ok;
+#if MBAR_SUSPEND_NS > 0
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity), "r"((uint32_t)MBAR_SUSPEND_NS)
+      : "memory");
+#else
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -77,6 +87,7 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t 
       : "=r"(ok)
       : "r"(smem_addr(bar)), "r"(parity)
       : "memory");
+#endif
   return ok != 0;
 }
 
@@ -117,6 +128,15 @@ enum { PM_SWEEP = 0, PM_RESID = 1, PM_SPMV = 2, PM_DOTS = 3, PM_RINIT = 4, PM_RT
 template <typename MT, int MODE, int PAT>
 __host__ __device__ constexpr bool pat_small() {
   return PAT > 0 && MODE != PM_DOTS;
+}
+
+// stages with the row-data area: the small pattern stages, and CSR sweeps and
+// residuals in standard stages of at most CSR_STAGE_ROWS rows (there the area
+// is small against the stage: 27-point levels, 64-row tiles)
+template <typename MT, int MODE, int PAT, int SB, int R>
+__host__ __device__ constexpr bool row_stage() {
+  return pat_small<MT, MODE, PAT>() ||
+         (PAT == 0 && SB == 1 && R <= CSR_STAGE_ROWS && (MODE == PM_SWEEP || MODE == PM_RESID));
 }
 
 template <typename MT, typename VT, typename OT>
@@ -231,17 +251,18 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
   pdl_trigger();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   constexpr bool SMALL = pat_small<MT, MODE, PAT>();
+  constexpr bool STG = row_stage<MT, MODE, PAT, SB, R>();
   constexpr int VB = (int)sizeof(VT);
   // staged row data of the small-stage forms: the row pointers (form 1) and
   // the row vectors the mode reads per row (slot 0 iterate, 1 right-hand
   // side or b, 2 D)
-  constexpr int NV = !SMALL ? 0
+  constexpr int NV = !STG ? 0
                      : MODE == PM_SWEEP ? 3
                      : (MODE == PM_RESID || MODE == PM_RINIT || MODE == PM_RTRUE || MODE == PM_RNORM) ? 1 : 0;
-  constexpr bool SRP = SMALL && PAT == 1;
+  constexpr bool SRP = STG && PAT != 2;
   const bool stg = (SRP || NV > 0) && a.stage_rows != 0;
-  auto* P = reinterpret_cast<PipeSmem<MT, S, SB, SMALL, VB, R>*>(smem_raw);
-  int32_t* tab = reinterpret_cast<int32_t*>(smem_raw + sizeof(PipeSmem<MT, S, SB, SMALL, VB, R>));  // PAT: offsets, lengths
+  auto* P = reinterpret_cast<PipeSmem<MT, S, SB, SMALL, VB, R, STG>*>(smem_raw);
+  int32_t* tab = reinterpret_cast<int32_t*>(smem_raw + sizeof(PipeSmem<MT, S, SB, SMALL, VB, R, STG>));  // PAT: offsets, lengths
   __shared__ double red[96];
   constexpr int VE = PipeTile<MT>::VE;
   constexpr int NCW = PIPE_CONSUMERS / 32;  // consumer warps
@@ -404,7 +425,7 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
         if (lane == 0) atomicOr(a.flags, ST_TIMEOUT);
         break;
       }
-      const PipeTile<MT, SB, SMALL, VB, R>& T = P->st[stage];
+      const PipeTile<MT, SB, SMALL, VB, R, STG>& T = P->st[stage];
       if (rows_staged) {
         p0 = T.rps[0];
         if (live) {
@@ -536,7 +557,8 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
 // and for the pattern forms the offset table (16-byte granules)
 template <typename MT, typename VT, int S, int SB, int MODE, int PAT, int R>
 static constexpr int pipe_smem(int tab_n) {
-  return (int)sizeof(PipeSmem<MT, S, SB, pat_small<MT, MODE, PAT>(), (int)sizeof(VT), R>) +
+  return (int)sizeof(PipeSmem<MT, S, SB, pat_small<MT, MODE, PAT>(), (int)sizeof(VT), R,
+                              row_stage<MT, MODE, PAT, SB, R>()>) +
          (PAT > 0 ? ((tab_n * 4 + 15) & ~15) : 0);
 }
 
@@ -557,7 +579,8 @@ static int pipe_grid(int n, int tab_n = 0) {
   int& bps = bps_by[PAT > 0 ? (tab_n * 4 + 255) / 256 : 0];
   if (bps <= 0) {  // sized for the table rounded up to its 256-byte step
     int b = 0;
-    const size_t occ = sizeof(PipeSmem<MT, S, SB, pat_small<MT, MODE, PAT>(), (int)sizeof(VT), R>) +
+    const size_t occ = sizeof(PipeSmem<MT, S, SB, pat_small<MT, MODE, PAT>(), (int)sizeof(VT), R,
+                                       row_stage<MT, MODE, PAT, SB, R>()>) +
                        (PAT > 0 ? (size_t)((tab_n * 4 + 255) & ~255) : 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, PIPE_CONSUMERS + 32, occ);
     bps = b < 1 ? 1 : b;

@@ -570,14 +570,16 @@ static inline void use_patterns(RowArgs<MT, VT, OT>& a, const Level& L, int form
 // threads per row / R = 256 with one); sb = 5: two consumer groups taking
 // tiles in turn, R = 128 rows with one thread per row, four 2x stages
 template <int MODE, typename MT, typename VT, typename OT>
-static void launch_rows(cudaStream_t s, int R, int sb, const RowArgs<MT, VT, OT>& a) {
+static void launch_rows(cudaStream_t s, int R, int sb, const RowArgs<MT, VT, OT>& a0) {
+  // the forms with a row-data area move the row pointers and row vectors by
+  // bulk copy where every source is 16-byte aligned (the library's own
+  // buffers are)
+  RowArgs<MT, VT, OT> b = a0;
+  auto al = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+  b.stage_rows = a0.stage_rows && al(a0.rp) && al(a0.x) && al(a0.r) && al(a0.dinv) && al(a0.b);
+  const RowArgs<MT, VT, OT>& a = b;
   if constexpr (MODE != PM_SWEEP_PROLONG) {  // latency-bound levels only: no pattern form
     if (a.pid) {
-      // small-stage forms move the row pointers and row vectors by bulk copy
-      // where every source is 16-byte aligned (the library's own buffers are)
-      RowArgs<MT, VT, OT> b = a;
-      auto al = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
-      b.stage_rows = a.stage_rows && al(a.rp) && al(a.x) && al(a.r) && al(a.dinv) && al(a.b);
       if (b.pcb) {  // one thread per row: R = 128 in two groups, or R = 256
         if (sb == 6) launch_pipe<1, 4, MODE, MT, VT, OT, 1, 2, 2>(s, b);
         else launch_pipe<1, 2, MODE, MT, VT, OT, 1, 1, 2>(s, b);
@@ -616,6 +618,7 @@ static void launch_sweep(cudaStream_t s, const Level& L, const MT* vals, const V
   const int R = L.R;
   if (L.pipe) {
     RowArgs<MT, VT, OT> a{L.n, L.rp, L.ci, vals, z, dinv, r, nullptr, nullptr, out, skip, nullptr, nullptr, nullptr, flags};
+    a.stage_rows = L.stage_rows ? 1 : 0;
     use_patterns(a, L, L.pat);
     launch_rows<PM_SWEEP>(s, R, L.sb, a);
     return;
@@ -665,6 +668,7 @@ static void launch_resid(cudaStream_t s, const Level& L, const MT* vals, const V
   const int R = L.R;
   if (L.pipe) {
     RowArgs<MT, VT, VT> a{L.n, L.rp, L.ci, vals, z, nullptr, r, nullptr, nullptr, t, skip, nullptr, nullptr, nullptr, flags};
+    a.stage_rows = L.stage_rows ? 1 : 0;
     use_patterns(a, L, L.pat);
     launch_rows<PM_RESID>(s, R, L.sb, a);
     return;
