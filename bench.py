@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -183,11 +184,19 @@ KERNEL_SOURCES = ("rows.cuh", "amg_internal.cuh")
 FP64_TFLOPS = 1.25
 
 
+def _code_only(text: str) -> str:
+    """The source without comments and with runs of whitespace collapsed, so
+    that a comment edit does not void a record of the compiled kernel."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_digest() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2303_02352_gb300", "csrc")
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(d, f), "rb").read())
+        h.update(_code_only(open(os.path.join(d, f)).read()).encode())
     return h.hexdigest()[:16]
 
 

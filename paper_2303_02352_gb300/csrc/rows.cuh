@@ -1,9 +1,11 @@
 // Persistent TMA-pipelined row kernels (included by solve.cu).
 //
 // A block owns tiles of R consecutive rows, round-robin over the grid.  The
-// nonzeros of a tile are contiguous in CSR; a producer warp issues two 1D bulk
+// nonzeros of a tile are contiguous in CSR; a producer warp issues 1D bulk
 // copies (cp.async.bulk, the TMA engine) that move the tile's values and column
-// indices into a shared-memory stage and signal the stage's "full" mbarrier.
+// indices (or, on pattern-coded levels, its one-byte row ids), and where the
+// stage has room its row pointers and row vectors, into a shared-memory stage
+// and signal the stage's "full" mbarrier.
 // S stages rotate: while the consumer warps compute tile k, the copies of the
 // next tiles are in flight, so HBM sees a continuous stream.  Each consumer
 // thread finishes one row (one multiply-add per nonzero, no shuffle reduction:
@@ -25,12 +27,11 @@
 // kernels need)
 // SB scales the stage: SB = 4 (FP64 only) holds 256 rows of up to 32 entries,
 // so long-row levels keep one thread per row (see launch_rows)
-// SMALL (pattern-coded columns): the same value capacity, room for the tile's
-// one-byte row ids instead of its column indices, and for the tile's row
-// pointers and up to three row vectors of VB bytes per entry (iterate,
-// right-hand side, D) of its RT rows, so that every stream of the row pass
-// arrives by bulk copy ahead of the consumers
-// (STG: the stage has the row-data area; PAT: the column area holds row ids)
+// PAT: the column area holds the tile's one-byte row ids (pattern-coded
+// columns; the same value capacity).  STG: the stage also has a row-data area
+// for the tile's row pointers and up to three row vectors of VB bytes per
+// entry (iterate, right-hand side, D) of its RT rows, so that every stream of
+// the row pass arrives by bulk copy ahead of the consumers.
 template <typename MT, int SB = 1, bool PAT = false, int VB = 8, int RT = PIPE_CONSUMERS, bool STG = PAT>
 struct PipeTile {
   static constexpr int VE = 16 / (int)sizeof(MT);
@@ -221,7 +222,7 @@ __device__ __forceinline__ bool mbar_wait_warp(unsigned long long* bar, uint32_t
 // rows; TPR threads share a row (entries strided by TPR, summed with shuffles),
 // so that long rows still keep every consumer busy per tile; TPR = 1 for short
 // rows (one thread per row).  Per stage a "full" barrier (the producer's
-// expect_tx plus the bytes of the two bulk copies) and an "empty" barrier (one
+// expect_tx plus the bytes of its bulk copies) and an "empty" barrier (one
 // arrival per consumer warp once it has read the stage).  No block-wide
 // barrier inside the tile loop: warps drift up to S tiles apart.
 //
@@ -253,9 +254,9 @@ __global__ void __launch_bounds__(PIPE_CONSUMERS + 32) k_rows_pipe(const RowArgs
   constexpr bool SMALL = pat_small<MT, MODE, PAT>();
   constexpr bool STG = row_stage<MT, MODE, PAT, SB, R>();
   constexpr int VB = (int)sizeof(VT);
-  // staged row data of the small-stage forms: the row pointers (form 1) and
-  // the row vectors the mode reads per row (slot 0 iterate, 1 right-hand
-  // side or b, 2 D)
+  // staged row data of the forms with a row-data area: the row pointers (CSR
+  // and form 1) and the row vectors the mode reads per row (slot 0 iterate,
+  // 1 right-hand side or b, 2 D)
   constexpr int NV = !STG ? 0
                      : MODE == PM_SWEEP ? 3
                      : (MODE == PM_RESID || MODE == PM_RINIT || MODE == PM_RTRUE || MODE == PM_RNORM) ? 1 : 0;
