@@ -162,7 +162,7 @@ struct amg_handle {
   int min_tpr = 1;             // tuning hook: least threads per row of the pipelined kernels
   int fuse = 1;                // restriction and prolongation fused into the coarse level's first / last sweep
   int use_big = 0;             // long-row form of the FP64 row kernels: 0 (off; measured best), 4 (4x stages, one thread per row), 2, 5
-  int use_ng = 2;              // levels with tiles of 32-128 rows in two consumer groups with half the threads per row (sb = 6): 0 none, 1 all kernels, 2 the FP64 outer kernels only (measured best)
+  int use_ng = 1;              // levels with tiles of 32-128 rows in two consumer groups with half the threads per row (sb = 6): 0 none, 1 all kernels (measured best with staged row data and the wait hint), 2 the FP64 outer kernels and pattern-coded float levels only
   int use_stage = 1;           // row data of the small-stage pattern kernels by bulk copy (0: the consumers load it)
   int use_pat = 1;             // pattern-coded columns on levels whose rows fall into at most 255 offset tuples: 0 never, 1 with row pointers (measured best), 2 with rows located from the tuple lengths where one thread takes a row
   int use_pair = 0;            // consecutive row passes in one launch (0 never: measured slower; 1 on levels with room for the lag; 2 always)

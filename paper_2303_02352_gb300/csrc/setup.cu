@@ -917,7 +917,10 @@ amg_status amg_finish_setup(amg_handle* h) {
       L.sbd = sbig;
     }
     // two consumer groups with half the threads per row (tiles of 32-128 rows):
-    // use_ng 1 on every kernel of the level, 2 on the FP64 outer kernels only
+    // use_ng 1 on every kernel of the level (27-point 128^3 FP64 solve 29.6 ->
+    // 28.1 ms, level-1 sweep 29.5 -> 24.4 us; 7-point log-normal 256^3 FP32
+    // 46.9 -> 46.3 ms; levels of 256-row tiles unchanged), 2 on the FP64 outer
+    // kernels only
     if (h->use_ng == 1 && L.pipe && L.sb == 1 && L.R >= 32 && L.R <= 128) L.sb = 6;
     if (h->use_ng >= 1 && L.piped && L.sbd == 1 && L.Rd >= 32 && L.Rd <= 128) L.sbd = 6;
     // pattern-coded columns (pattern.cu), read by the pipelined forms that have
@@ -926,10 +929,9 @@ amg_status amg_finish_setup(amg_handle* h) {
       amg_status sp = amg_build_patterns(h, k);
       if (sp != AMG_OK) return sp;
     }
-    // pattern-coded float levels with tiles of 32-128 rows: two consumer groups
-    // with half the threads per row (27-point 128^3 FP32 level-0 sweep 75.4 ->
-    // 56.4 us, solve 17.3 -> 16.0 ms; on FP64 levels the form is mixed and
-    // stays off, use_ng above)
+    // pattern-coded float levels with tiles of 32-128 rows take two consumer
+    // groups with use_ng 2 as well (27-point 128^3 FP32 level-0 sweep 75.4 ->
+    // 56.4 us, solve 17.3 -> 16.0 ms)
     if (h->use_ng >= 1 && L.pid && vb < 8 && L.pipe && L.sb == 1 && L.R >= 32 && L.R <= 128) L.sb = 6;
     // FP64 forms with several threads per row (27-point levels) keep CSR
     // columns: FP64-issue bound, their kernels gain nothing from fewer bytes
