@@ -187,6 +187,31 @@ def test_staged_row_data_equals_loaded_row_data(name, prec, monkeypatch):
     assert np.array_equal(rg["x"].cpu().numpy(), rc["x"].cpu().numpy())
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_per_row_damping_on_pattern_coded_levels(prec, monkeypatch):
+    """Per-row damping (the learned smoother's D = omega / l1) on pattern-coded
+    levels with staged row data: against the oracle with the same omegas (FP64,
+    1e-12) and bitwise against CSR columns with the same omegas."""
+    A = STENCILS["diff7_48"]()
+    g = G(A, precision=prec)
+    assert g.info()["column_form"][0] == 1
+    monkeypatch.setenv("AMG_PAT", "0")
+    c = G(A, precision=prec)
+    rng = np.random.default_rng(7)
+    oms = [0.6 + 0.8 * rng.random(n) for n in g.info()["n"]]
+    for k, om in enumerate(oms):
+        g.set_omega(k, om)
+        c.set_omega(k, om)
+    r = W.random_vector(A.n, 21)
+    zg = g.vcycle(r).cpu().numpy()
+    assert np.array_equal(zg, c.vcycle(r).cpu().numpy())
+    if prec == 0:
+        o = O.Hierarchy(A)
+        for k, om in enumerate(oms):
+            o.set_omega(k, om)
+        assert rel(zg, o.vcycle(r)) < 1e-12
+
+
 @pytest.mark.parametrize("dmax, singleton, expect", [(127, True, 255), (128, False, 0)])
 def test_tuple_count_boundary(dmax, singleton, expect, monkeypatch):
     """255 distinct offset tuples take the pattern form (ids 0 .. 254), 256
