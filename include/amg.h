@@ -120,7 +120,11 @@ void amg_params_default(amg_params* p);
 /*
  * Builds the hierarchy on the GPU (Alg. 3, Sec. 3.1): matching weights, suitor
  * matching with an index tie-break, pairwise aggregation, Galerkin products,
- * s-fold composition, l1-Jacobi diagonals, low-precision copies.
+ * s-fold composition, l1-Jacobi diagonals, low-precision copies.  It also
+ * stores, for each level of at least 32,768 rows whose rows fall into at most
+ * 255 distinct tuples of column offsets, a one-byte tuple id per row that the
+ * solve-phase row kernels read instead of the column indices (the same
+ * matrix: entries, order and results unchanged; amg_info_t column_patterns).
  * A: device CSR, read during the call only (deep-copied).  p: NULL = defaults.
  * stream: a cudaStream_t (may be NULL).  *out receives the handle.
  * Errors: AMG_ERR_INVALID_ARG (structure, asymmetry, NaN), AMG_ERR_NOT_SPD
