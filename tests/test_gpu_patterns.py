@@ -165,6 +165,47 @@ def test_per_row_damping_on_pattern_coded_levels(prec, monkeypatch):
         assert rel(zg, o.vcycle(r)) < 1e-12
 
 
+VARIANTS = {"w_cycle": dict(cycle=2), "jacobi": dict(relax_type=0), "decoupled3": dict(num_parts=3),
+            "w_normalised": dict(prolong_scale=1)}
+
+
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
+def test_method_variants_on_pattern_coded_levels(variant, monkeypatch):
+    """The method variants on a pattern-coded hierarchy (59,319 rows, an odd
+    grid: aggregates of unequal sizes, so the w-normalised prolongator and the
+    3 row blocks change the operator): V-cycle within 1e-12 of the oracle's
+    same variant and bitwise equal to CSR columns."""
+    kw = VARIANTS[variant]
+    A = W.poisson7(39)
+    g = G(A, **kw)
+    assert g.info()["column_form"][0] == 1
+    okw = dict(kw)
+    if "prolong_scale" in okw:
+        okw["prolong_scale"] = O.PROLONG_W_NORMALIZED
+    o = O.Hierarchy(A, **okw)
+    r = W.random_vector(A.n, 31)
+    zg = g.vcycle(r).cpu().numpy()
+    assert rel(zg, o.vcycle(r)) < 1e-12
+    monkeypatch.setenv("AMG_PAT", "0")
+    assert np.array_equal(zg, G(A, **kw).vcycle(r).cpu().numpy())
+
+
+def test_checkpoint_of_a_pattern_coded_hierarchy(tmp_path):
+    """A saved hierarchy rebuilds the same pattern-coded columns when loaded:
+    the same tuple counts and a bitwise equal V-cycle."""
+    from paper_2303_02352_gb300 import amg
+    A = W.poisson7(40)
+    g = G(A)
+    path = str(tmp_path / "poisson40.amgh")
+    g.save(path)
+    h = amg.Hierarchy.load(path)
+    assert h.info()["column_patterns"] == g.info()["column_patterns"]
+    assert h.info()["column_patterns"][0] == 27
+    r = W.random_vector(A.n, 32)
+    assert np.array_equal(g.vcycle(r).cpu().numpy(), h.vcycle(r).cpu().numpy())
+    h.close()
+
+
 @pytest.mark.parametrize("dmax, singleton, expect", [(127, True, 255), (128, False, 0)])
 def test_tuple_count_boundary(dmax, singleton, expect, monkeypatch):
     """255 distinct offset tuples take the pattern form (ids 0 .. 254), 256
